@@ -1,0 +1,997 @@
+// Host runtime and C ABI (include/extraferm.h).
+//
+// Host preprocessing in FP64 (Section IV-A: sin/cos tables precomputed once):
+//   * controlled-phase tables: wrapped angle, c = cos(theta/4), s = sin(theta/4)
+//     (Eq. 7), sampling threshold T = round(p(x=1) 2^32) (Eqs. 10-12);
+//   * independent mode blocks: modes joined by Givens rotations; at most two
+//     blocks holding particles are kept apart (more are merged into one);
+//   * per block, the passive segments S_0..S_L between the runs of
+//     controlled-phase gates that touch the block, and T_l = S_l diag(base
+//     phases e^{i theta/2} of layer l) (Section IV-B, Eqs. 14-18);
+//   * Exact: sub-branch bit layout, flip masks and weight tables;
+//   * Raw Estimate: interval products Pi_{a..b} = T_a ... T_b.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ef_internal.h"
+#include "extraferm.h"
+
+using cd = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define EF_CK(call)                                                                              \
+    do {                                                                                         \
+        cudaError_t _e = (call);                                                                 \
+        if (_e != cudaSuccess)                                                                   \
+            return fail(EF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));           \
+    } while (0)
+
+constexpr double kTwo32 = 4294967296.0;
+constexpr double kPi = 3.14159265358979323846;
+
+double wrap_angle(double theta) {
+    double t = theta - 2.0 * kPi * std::floor((theta + kPi) / (2.0 * kPi));
+    if (t <= -kPi) t += 2.0 * kPi;
+    return t;
+}
+
+struct CP {
+    int gate, p, q;
+    double theta, c, s, pT0, pT1, ratio0, ratio1;
+    uint32_t T;
+    int blk_p, blk_q;  // active block of each mode (-1 = none)
+    int cls;           // -1 free, 0/1 local to block, 2 shared
+};
+
+// A device buffer that only grows.
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want) {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(want, 256));
+        if (e == cudaSuccess) bytes = std::max<size_t>(want, 256);
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+template <typename T>
+cudaError_t upload(DBuf& d, const std::vector<T>& h, cudaStream_t s) {
+    cudaError_t e = d.ensure(h.size() * sizeof(T));
+    if (e != cudaSuccess || h.empty()) return e;
+    return cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+struct HostBlock {
+    int n = 0, eta = 0, L = 0;
+    uint64_t mask[2] = {0, 0};
+    std::vector<int> modes;  // local -> global
+    std::vector<int> cols;   // occupied local modes
+    std::vector<std::vector<int>> layers;  // cphase indices per layer (1..L -> [0..L-1])
+    std::vector<cd> S;       // (L+1) n x n segments
+    std::vector<cd> T;       // (L+1) n x n: T_0 = S_0, T_l = S_l diag(D_l0)
+    // Exact
+    int k_loc = 0;
+    std::vector<int> local_gates;  // cphase indices, bits 0..k_loc-1
+    std::vector<uint32_t> F;       // L x n
+    std::vector<double> WLlo, WLhi;
+    int lobits = 0;
+    int c_log2 = 0;
+    // Raw Estimate
+    std::vector<cd> P;   // tri(L) x n x n
+    std::vector<cd> RC;  // L x n x eta
+    // device
+    DBuf dS0C, dT, dF, dWLlo, dWLhi, dM64, dM32, dPart, dP64, dP32, dRC64, dRC32, dCols;
+    void release() {
+        for (DBuf* b : {&dS0C, &dT, &dF, &dWLlo, &dWLhi, &dM64, &dM32, &dPart, &dP64, &dP32, &dRC64, &dRC32, &dCols})
+            b->release();
+    }
+};
+
+int tri(int a, int b) { return a * (a + 1) / 2 + b; }
+
+void split_table(const std::vector<double>& factors0, const std::vector<double>& factors1, int& lobits,
+                 std::vector<double>& lo, std::vector<double>& hi) {
+    // w(y) = prod_i (bit_i ? factors1[i] : factors0[i]) = lo[y & (2^lobits-1)] * hi[y >> lobits]
+    const int k = (int)factors0.size();
+    lobits = k / 2;
+    const int hib = k - lobits;
+    lo.assign((size_t)1 << lobits, 1.0);
+    hi.assign((size_t)1 << hib, 1.0);
+    for (size_t y = 0; y < lo.size(); ++y)
+        for (int i = 0; i < lobits; ++i) lo[y] *= ((y >> i) & 1) ? factors1[i] : factors0[i];
+    for (size_t y = 0; y < hi.size(); ++y)
+        for (int i = 0; i < hib; ++i) hi[y] *= ((y >> i) & 1) ? factors1[lobits + i] : factors0[lobits + i];
+}
+
+double log_binom(int n, int k) { return std::lgamma(n + 1.0) - std::lgamma(k + 1.0) - std::lgamma(n - k + 1.0); }
+
+}  // namespace
+
+struct ef_circuit {
+    int n = 0;
+    uint64_t occ[2] = {0, 0};
+    std::vector<ef_gate> gates;
+    ef_options opt{};
+    int device = 0;
+
+    // derived
+    std::vector<CP> cps;
+    double xi = 1.0;
+    int nblocks = 0;
+    HostBlock blk[ef::kMaxBlocks];
+    uint64_t inactive[2] = {0, 0};
+    std::vector<int> shared_gates;
+    std::vector<double> WSlo, WShi;
+    int shlobits = 0;
+    bool exact_ok = true;
+    std::string exact_why;
+    bool approx_ok = true;
+    std::string approx_why;
+    double p_floor = 0.0;
+    // Raw Estimate gate tables
+    std::vector<uint32_t> aT;
+    std::vector<double> aq;
+    std::vector<uint8_t> alayer;
+    std::vector<uint64_t> amodes;
+    double R0 = 1.0;
+
+    bool dirty = true;
+    DBuf dWSlo, dWShi, dList, dListCount, dMaxErr, dBits, dOut, dErr, dGradP, dGrad;
+    DBuf daT, daq, dalayer, damodes, daPart, dCounters;
+    cudaStream_t own_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+    cudaStream_t last_stream = nullptr;
+    ef_stats stats{};
+    int64_t last_fp64_list_pending = 0;  // 1 if the fp64 list count must be read back
+    int64_t last_sub_total = 0;          // sum over blocks of 2^k_B (for executed-LU accounting)
+    int last_mode = 0;                   // 1 exact, 2 approx
+
+    ~ef_circuit() {
+        for (int b = 0; b < ef::kMaxBlocks; ++b) blk[b].release();
+        for (DBuf* d : {&dWSlo, &dWShi, &dList, &dListCount, &dMaxErr, &dBits, &dOut, &dErr, &dGradP, &dGrad, &daT,
+                        &daq, &dalayer, &damodes, &daPart, &dCounters})
+            d->release();
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (own_stream) cudaStreamDestroy(own_stream);
+    }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ preprocessing
+
+int prepare(ef_circuit* c) {
+    const int n = c->n;
+    // controlled-phase tables
+    c->cps.clear();
+    c->xi = 1.0;
+    for (size_t gi = 0; gi < c->gates.size(); ++gi) {
+        const ef_gate& g = c->gates[gi];
+        if (g.kind != EF_CPHASE) continue;
+        CP cp{};
+        cp.gate = (int)gi;
+        cp.p = g.p;
+        cp.q = g.q;
+        cp.theta = wrap_angle(g.theta);
+        cp.c = std::cos(cp.theta / 4.0);
+        cp.s = std::sin(cp.theta / 4.0);
+        const double sa = std::sin(std::fabs(cp.theta) / 4.0), ca = std::cos(std::fabs(cp.theta) / 4.0);
+        const double p1 = sa / (sa + ca);
+        uint64_t T = 0;
+        if (sa != 0.0) {
+            T = (uint64_t)std::floor(p1 * kTwo32 + 0.5);
+            T = std::min<uint64_t>(std::max<uint64_t>(T, 1), 4294967295ull);
+        }
+        cp.T = (uint32_t)T;
+        cp.pT1 = (double)T / kTwo32;
+        cp.pT0 = 1.0 - cp.pT1;
+        cp.ratio0 = cp.c / cp.pT0;
+        cp.ratio1 = T > 0 ? cp.s / cp.pT1 : 0.0;
+        c->xi *= (ca + sa) * (ca + sa);
+        c->cps.push_back(cp);
+    }
+    const int k = (int)c->cps.size();
+
+    // components joined by Givens rotations (adjacent modes -> intervals)
+    std::vector<int> comp(n);
+    {
+        std::vector<char> join(n, 0);  // join[m]: m and m+1 connected
+        for (const ef_gate& g : c->gates)
+            if (g.kind == EF_GIVENS) join[g.p] = 1;
+        int id = 0;
+        for (int m = 0; m < n; ++m) {
+            comp[m] = id;
+            if (!(m + 1 < n && join[m])) ++id;
+        }
+    }
+    const int ncomp = comp[n - 1] + 1;
+    std::vector<int> comp_eta(ncomp, 0);
+    for (int m = 0; m < n; ++m)
+        if ((c->occ[m >> 6] >> (m & 63)) & 1ull) comp_eta[comp[m]]++;
+    std::vector<int> active;
+    for (int i = 0; i < ncomp; ++i)
+        if (comp_eta[i] > 0) active.push_back(i);
+    std::vector<int> block_of_comp(ncomp, -1);
+    if (active.size() <= (size_t)ef::kMaxBlocks) {
+        for (size_t i = 0; i < active.size(); ++i) block_of_comp[active[i]] = (int)i;
+        c->nblocks = (int)active.size();
+    } else {
+        for (int a : active) block_of_comp[a] = 0;
+        c->nblocks = 1;
+    }
+    std::vector<int> block_of(n), local_of(n, -1);
+    c->inactive[0] = c->inactive[1] = 0;
+    for (int b = 0; b < ef::kMaxBlocks; ++b) {
+        HostBlock& B = c->blk[b];
+        B.modes.clear();
+        B.cols.clear();
+        B.mask[0] = B.mask[1] = 0;
+    }
+    for (int m = 0; m < n; ++m) {
+        const int b = block_of_comp[comp[m]];
+        block_of[m] = b;
+        if (b < 0) {
+            c->inactive[m >> 6] |= 1ull << (m & 63);
+            continue;
+        }
+        HostBlock& B = c->blk[b];
+        local_of[m] = (int)B.modes.size();
+        if ((c->occ[m >> 6] >> (m & 63)) & 1ull) B.cols.push_back(local_of[m]);
+        B.modes.push_back(m);
+        B.mask[m >> 6] |= 1ull << (m & 63);
+    }
+    for (int b = 0; b < c->nblocks; ++b) {
+        c->blk[b].n = (int)c->blk[b].modes.size();
+        c->blk[b].eta = (int)c->blk[b].cols.size();
+    }
+    // gate classes
+    c->shared_gates.clear();
+    for (int j = 0; j < k; ++j) {
+        CP& cp = c->cps[j];
+        cp.blk_p = block_of[cp.p];
+        cp.blk_q = block_of[cp.q];
+        if (cp.blk_p < 0 && cp.blk_q < 0) cp.cls = -1;
+        else if (cp.blk_p >= 0 && cp.blk_q >= 0 && cp.blk_p != cp.blk_q) cp.cls = 2;
+        else cp.cls = cp.blk_p >= 0 ? cp.blk_p : cp.blk_q;
+        if (cp.cls == 2) c->shared_gates.push_back(j);
+    }
+    const int k_sh = (int)c->shared_gates.size();
+
+    c->exact_ok = true;
+    c->exact_why.clear();
+    c->approx_ok = true;
+    c->approx_why.clear();
+    double log_sector = 0.0;
+    c->alayer.assign((size_t)ef::kMaxBlocks * k, 0);
+    c->amodes.assign((size_t)ef::kMaxBlocks * k, 0);
+
+    // per-block segments, layers and tables
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        const int nb_ = B.n;
+        log_sector += log_binom(B.n, B.eta);
+        auto eye = [&]() {
+            std::vector<cd> I((size_t)nb_ * nb_, cd(0, 0));
+            for (int i = 0; i < nb_; ++i) I[(size_t)i * nb_ + i] = 1.0;
+            return I;
+        };
+        std::vector<std::vector<cd>> segs;
+        B.layers.clear();
+        std::vector<cd> seg = eye();
+        bool in_layer = false;
+        std::vector<int> cur;
+        int j = 0;
+        std::vector<int> layer_of_cp(k, 0);
+        for (const ef_gate& g : c->gates) {
+            if (g.kind == EF_CPHASE) {
+                const CP& cp = c->cps[j];
+                const bool touches = cp.blk_p == b || cp.blk_q == b;
+                if (touches) {
+                    if (!in_layer) {
+                        segs.push_back(seg);
+                        in_layer = true;
+                        cur.clear();
+                    }
+                    cur.push_back(j);
+                    layer_of_cp[j] = (int)B.layers.size() + 1;
+                }
+                ++j;
+                continue;
+            }
+            if (block_of[g.p] != b) continue;
+            if (in_layer) {
+                B.layers.push_back(cur);
+                in_layer = false;
+                seg = eye();
+            }
+            const int lp = local_of[g.p];
+            if (g.kind == EF_GIVENS) {
+                const int lq = local_of[g.q];
+                const double ct = std::cos(g.theta), st = std::sin(g.theta);
+                const cd e = std::polar(1.0, g.phi), em = std::polar(1.0, -g.phi);
+                const cd g00 = ct, g01 = -e * st, g10 = em * st, g11 = ct;
+                for (int col = 0; col < nb_; ++col) {
+                    const cd a = seg[(size_t)lp * nb_ + col], bb = seg[(size_t)lq * nb_ + col];
+                    seg[(size_t)lp * nb_ + col] = g00 * a + g01 * bb;
+                    seg[(size_t)lq * nb_ + col] = g10 * a + g11 * bb;
+                }
+            } else {  // PHASE
+                const cd e = std::polar(1.0, g.phi);
+                for (int col = 0; col < nb_; ++col) seg[(size_t)lp * nb_ + col] *= e;
+            }
+        }
+        if (in_layer) {
+            B.layers.push_back(cur);
+            seg = eye();
+        }
+        segs.push_back(seg);
+        B.L = (int)B.layers.size();
+        const int L = B.L;
+        const size_t nn = (size_t)nb_ * nb_;
+        B.S.assign((size_t)(L + 1) * nn, cd(0, 0));
+        B.T.assign((size_t)(L + 1) * nn, cd(0, 0));
+        for (int l = 0; l <= L; ++l) std::copy(segs[l].begin(), segs[l].end(), B.S.begin() + l * nn);
+        // T_0 = S_0; T_l = S_l diag(base phases of layer l)
+        std::copy(segs[0].begin(), segs[0].end(), B.T.begin());
+        for (int l = 1; l <= L; ++l) {
+            std::vector<cd> d(nb_, cd(1, 0));
+            for (int jj : B.layers[l - 1]) {
+                const CP& cp = c->cps[jj];
+                const cd ph = std::polar(1.0, 0.5 * cp.theta);
+                if (cp.blk_p == b) d[local_of[cp.p]] *= ph;
+                if (cp.blk_q == b) d[local_of[cp.q]] *= ph;
+            }
+            for (int i = 0; i < nb_; ++i)
+                for (int m = 0; m < nb_; ++m) B.T[l * nn + (size_t)i * nb_ + m] = segs[l][(size_t)i * nb_ + m] * d[m];
+        }
+
+        // ---- Exact: local gate bits, flip masks, weight tables
+        B.local_gates.clear();
+        for (int jj = 0; jj < k; ++jj)
+            if (c->cps[jj].cls == b) B.local_gates.push_back(jj);
+        B.k_loc = (int)B.local_gates.size();
+        const int kB = B.k_loc + (c->nblocks == 2 ? k_sh : 0);
+        if (kB > ef::kMaxExactSubBits) {
+            c->exact_ok = false;
+            c->exact_why = "Exact mode: a mode block has " + std::to_string(kB) +
+                           " controlled-phase gates; this build enumerates at most 2^" +
+                           std::to_string(ef::kMaxExactSubBits) + " sub-branches per block";
+        }
+        if (B.eta > ef::kMaxEtaRows) {
+            c->exact_ok = false;
+            c->exact_why = "Exact mode: more than 32 particles in one mode block";
+        }
+        std::vector<int> ybit(k, -1);
+        for (int i = 0; i < B.k_loc; ++i) ybit[B.local_gates[i]] = i;
+        if (c->nblocks == 2)
+            for (int i = 0; i < k_sh; ++i) ybit[c->shared_gates[i]] = B.k_loc + i;
+        B.F.assign((size_t)L * nb_, 0u);
+        for (int l = 1; l <= L; ++l)
+            for (int jj : B.layers[l - 1]) {
+                const CP& cp = c->cps[jj];
+                if (ybit[jj] < 0 || ybit[jj] >= 32) continue;
+                const uint32_t bit = 1u << ybit[jj];
+                if (cp.blk_p == b) B.F[(size_t)(l - 1) * nb_ + local_of[cp.p]] ^= bit;
+                if (cp.blk_q == b) B.F[(size_t)(l - 1) * nb_ + local_of[cp.q]] ^= bit;
+            }
+        if (kB <= ef::kMaxExactSubBits) {
+            std::vector<double> f0, f1;
+            for (int jj : B.local_gates) {
+                f0.push_back(c->cps[jj].c);
+                f1.push_back(c->cps[jj].s);
+            }
+            split_table(f0, f1, B.lobits, B.WLlo, B.WLhi);
+        } else {
+            B.WLlo.assign(1, 1.0);
+            B.WLhi.assign(1, 1.0);
+            B.lobits = 0;
+        }
+        // chunk of sub-branches handled per FP32 CTA: fit the chunk in 48 KB of shared memory
+        {
+            int cl = std::min(B.k_loc, 5);
+            if (c->opt.tile_override[0] > 0) cl = std::min(B.k_loc, c->opt.tile_override[0]);
+            if (B.eta <= ef::kMaxEtaThread)
+                while (cl > 0 && ((size_t)1 << cl) * nb_ * (size_t)(B.eta | 1) * 8 > 48 * 1024) --cl;
+            B.c_log2 = cl;
+        }
+
+        // ---- Raw Estimate: interval products and right factors
+        B.P.assign((size_t)(tri(L, L) + 1) * nn, cd(0, 0));
+        for (int bb = 0; bb <= L; ++bb) {
+            // Pi_{bb..bb} = T_bb; Pi_{a..bb} = T_a Pi_{a-1..bb}
+            std::copy(B.T.begin() + bb * nn, B.T.begin() + (bb + 1) * nn, B.P.begin() + (size_t)tri(bb, bb) * nn);
+            for (int a = bb + 1; a <= L; ++a) {
+                const cd* Ta = &B.T[a * nn];
+                const cd* prev = &B.P[(size_t)tri(a - 1, bb) * nn];
+                cd* out = &B.P[(size_t)tri(a, bb) * nn];
+                for (int i = 0; i < nb_; ++i)
+                    for (int jj = 0; jj < nb_; ++jj) {
+                        cd acc = 0;
+                        for (int m = 0; m < nb_; ++m) acc += Ta[(size_t)i * nb_ + m] * prev[(size_t)m * nb_ + jj];
+                        out[(size_t)i * nb_ + jj] = acc;
+                    }
+            }
+        }
+        B.RC.assign((size_t)L * nb_ * B.eta, cd(0, 0));
+        for (int l = 0; l < L; ++l) {
+            const cd* Pl0 = &B.P[(size_t)tri(l, 0) * nn];
+            for (int i = 0; i < nb_; ++i)
+                for (int cc = 0; cc < B.eta; ++cc)
+                    B.RC[((size_t)l * nb_ + i) * B.eta + cc] = Pl0[(size_t)i * nb_ + B.cols[cc]];
+        }
+        if (B.eta > ef::kMaxApproxEta) {
+            c->approx_ok = false;
+            c->approx_why = "Raw Estimate: more than 8 particles in one mode block";
+        }
+        if (L > ef::kMaxApproxLayers || nb_ > 64 || (L > 0 && (L - 1) * nb_ > ef::kMaxApproxStored)) {
+            c->approx_ok = false;
+            c->approx_why = "Raw Estimate: mode block with more than 64 modes, more than 8 controlled-phase "
+                            "layers, or (layers-1)*modes above 64";
+        }
+        for (int jj = 0; jj < k; ++jj) {
+            const CP& cp = c->cps[jj];
+            uint64_t mm = 0;
+            if (cp.blk_p == b) mm ^= 1ull << local_of[cp.p];
+            if (cp.blk_q == b) mm ^= 1ull << local_of[cp.q];
+            c->alayer[(size_t)b * k + jj] = (uint8_t)((cp.blk_p == b || cp.blk_q == b) ? layer_of_cp[jj] : 0);
+            c->amodes[(size_t)b * k + jj] = (nb_ <= 64) ? mm : 0;
+        }
+    }
+    // shared weight table
+    if (k_sh <= ef::kMaxExactSubBits) {
+        std::vector<double> f0, f1;
+        if (c->nblocks == 2)
+            for (int jj : c->shared_gates) {
+                f0.push_back(c->cps[jj].c);
+                f1.push_back(c->cps[jj].s);
+            }
+        split_table(f0, f1, c->shlobits, c->WSlo, c->WShi);
+    } else {
+        c->WSlo.assign(1, 1.0);
+        c->WShi.assign(1, 1.0);
+        c->shlobits = 0;
+    }
+    c->p_floor = 1e-6 * std::exp(-log_sector);
+    // approx gate tables
+    c->aT.assign(k, 0);
+    c->aq.assign(k, 0.0);
+    c->R0 = 1.0;
+    for (int jj = 0; jj < k; ++jj) {
+        const CP& cp = c->cps[jj];
+        c->aT[jj] = cp.T;
+        c->aq[jj] = cp.ratio0 != 0.0 ? cp.ratio1 / cp.ratio0 : 0.0;
+        c->R0 *= cp.ratio0;
+    }
+    c->dirty = true;
+    return EF_OK;
+}
+
+int upload_tables(ef_circuit* c, cudaStream_t s) {
+    if (!c->dirty) return EF_OK;
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        const size_t nn = (size_t)B.n * B.n;
+        std::vector<double2> S0C((size_t)B.n * B.eta), T((size_t)B.L * nn);
+        for (int i = 0; i < B.n; ++i)
+            for (int cc = 0; cc < B.eta; ++cc) {
+                const cd v = B.S[(size_t)i * B.n + B.cols[cc]];
+                S0C[(size_t)i * B.eta + cc] = make_double2(v.real(), v.imag());
+            }
+        for (size_t e = 0; e < (size_t)B.L * nn; ++e) T[e] = make_double2(B.T[nn + e].real(), B.T[nn + e].imag());
+        EF_CK(upload(B.dS0C, S0C, s));
+        EF_CK(upload(B.dT, T, s));
+        EF_CK(upload(B.dF, B.F, s));
+        EF_CK(upload(B.dWLlo, B.WLlo, s));
+        EF_CK(upload(B.dWLhi, B.WLhi, s));
+        std::vector<double2> P64(B.P.size()), RC64(B.RC.size());
+        std::vector<float2> P32(B.P.size()), RC32(B.RC.size());
+        for (size_t e = 0; e < B.P.size(); ++e) {
+            P64[e] = make_double2(B.P[e].real(), B.P[e].imag());
+            P32[e] = make_float2((float)B.P[e].real(), (float)B.P[e].imag());
+        }
+        for (size_t e = 0; e < B.RC.size(); ++e) {
+            RC64[e] = make_double2(B.RC[e].real(), B.RC[e].imag());
+            RC32[e] = make_float2((float)B.RC[e].real(), (float)B.RC[e].imag());
+        }
+        EF_CK(upload(B.dP64, P64, s));
+        EF_CK(upload(B.dP32, P32, s));
+        EF_CK(upload(B.dRC64, RC64, s));
+        EF_CK(upload(B.dRC32, RC32, s));
+        EF_CK(upload(B.dCols, B.cols, s));
+    }
+    EF_CK(upload(c->dWSlo, c->WSlo, s));
+    EF_CK(upload(c->dWShi, c->WShi, s));
+    std::vector<uint32_t> T4(((c->aT.size() + 3) & ~(size_t)3), 0u);
+    std::copy(c->aT.begin(), c->aT.end(), T4.begin());
+    EF_CK(upload(c->daT, T4, s));
+    EF_CK(upload(c->daq, c->aq, s));
+    EF_CK(upload(c->dalayer, c->alayer, s));
+    EF_CK(upload(c->damodes, c->amodes, s));
+    c->dirty = false;
+    return EF_OK;
+}
+
+int validate_gates(int n, const ef_gate* gates, int64_t ng) {
+    for (int64_t i = 0; i < ng; ++i) {
+        const ef_gate& g = gates[i];
+        const std::string at = "gate " + std::to_string(i) + ": ";
+        if (g.reserved != 0) return fail(EF_EINVAL, at + "reserved field must be 0");
+        if (g.p < 0 || g.p >= n) return fail(EF_EINVAL, at + "mode p out of range");
+        switch (g.kind) {
+            case EF_GIVENS:
+                if (g.q != g.p + 1 || g.q >= n)
+                    return fail(EF_EINVAL, at + "Givens rotations act on adjacent modes (q = p + 1 < n)");
+                if (!std::isfinite(g.theta) || !std::isfinite(g.phi)) return fail(EF_EINVAL, at + "non-finite angle");
+                break;
+            case EF_PHASE:
+                if (!std::isfinite(g.phi)) return fail(EF_EINVAL, at + "non-finite angle");
+                break;
+            case EF_CPHASE:
+                if (g.q < 0 || g.q >= n || g.q == g.p) return fail(EF_EINVAL, at + "controlled phase needs p != q < n");
+                if (!std::isfinite(g.theta)) return fail(EF_EINVAL, at + "non-finite angle");
+                break;
+            default:
+                return fail(EF_EINVAL, at + "unknown gate kind");
+        }
+    }
+    return EF_OK;
+}
+
+double lu_flops(int eta) {
+    double f = 17.0 * eta;
+    for (int k = 0; k < eta; ++k) {
+        const double r = eta - k - 1;
+        f += 8.0 * r * r + 6.0 * r;
+    }
+    return f;
+}
+
+int begin_call(ef_circuit* c, cudaStream_t s, int mode) {
+    if (c->last_stream && c->last_stream != s) EF_CK(cudaStreamSynchronize(c->last_stream));
+    c->last_stream = s;
+    c->stats = ef_stats{};
+    c->last_mode = mode;
+    c->last_fp64_list_pending = 0;
+    c->timed = (c->opt.flags & EF_FLAG_TIME_KERNELS) != 0;
+    if (c->timed && !c->ev0) {
+        EF_CK(cudaEventCreate(&c->ev0));
+        EF_CK(cudaEventCreate(&c->ev1));
+    }
+    return upload_tables(c, s);
+}
+
+ef::ExactBlockDev exact_block_dev(ef_circuit* c, int b) {
+    HostBlock& B = c->blk[b];
+    ef::ExactBlockDev d{};
+    d.n = B.n;
+    d.eta = B.eta;
+    d.L = B.L;
+    d.k_loc = B.k_loc;
+    d.k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
+    d.c_log2 = B.c_log2;
+    d.lobits = B.lobits;
+    d.mask0 = B.mask[0];
+    d.mask1 = B.mask[1];
+    d.S0C = B.dS0C.as<double2>();
+    d.T = B.dT.as<double2>();
+    d.F = B.dF.as<uint32_t>();
+    d.WLlo = B.dWLlo.as<double>();
+    d.WLhi = B.dWLhi.as<double>();
+    d.M64 = B.dM64.as<double2>();
+    d.M32 = B.dM32.as<float2>();
+    d.part = B.dPart.as<ef::d4>();
+    d.n_chunks = 1 << (d.k_loc + d.k_sh - d.c_log2);
+    return d;
+}
+
+int exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out, double* d_err, cudaStream_t s) {
+    if (!c->exact_ok) return fail(EF_EUNSUPPORTED, c->exact_why);
+    int rc = begin_call(c, s, 1);
+    if (rc) return rc;
+    const int prec = c->opt.precision;
+    const bool fp64_only = prec == EF_PREC_FP64;
+    ef::LaunchStats st;
+    c->stats.logical_branch_dets = nb * (int64_t)std::ldexp(1.0, (int)c->cps.size());
+    if (nb == 0) return EF_OK;
+    // workspaces
+    double flops = 0.0;
+    int64_t sub_total = 0;
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        const int kB = B.k_loc + (c->nblocks == 2 ? (int)c->shared_gates.size() : 0);
+        const size_t ny = (size_t)1 << kB;
+        const size_t ne = (size_t)B.n * B.eta;
+        EF_CK(B.dM64.ensure(ny * ne * sizeof(double2)));
+        if (!fp64_only) EF_CK(B.dM32.ensure(ny * ne * sizeof(float2)));
+        const size_t nch = (size_t)1 << (kB - B.c_log2);
+        EF_CK(B.dPart.ensure(nch * (size_t)nb * sizeof(ef::d4)));
+        flops += (double)nb * (double)ny * lu_flops(B.eta);
+        sub_total += (int64_t)ny;
+    }
+    c->last_sub_total = sub_total;
+    // builder
+    for (int b = 0; b < c->nblocks; ++b) {
+        ef::ExactBlockDev d = exact_block_dev(c, b);
+        EF_CK(ef::launch_build_branches(d, !fp64_only, s, st));
+    }
+    ef::ExactCombineDev cm{};
+    cm.nblocks = c->nblocks;
+    cm.k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
+    cm.shlobits = c->shlobits;
+    cm.WSlo = c->dWSlo.as<double>();
+    cm.WShi = c->dWShi.as<double>();
+    cm.inactive0 = c->inactive[0];
+    cm.inactive1 = c->inactive[1];
+    cm.eta_max = 0;
+    for (int b = 0; b < c->nblocks; ++b) {
+        cm.mask[b][0] = c->blk[b].mask[0];
+        cm.mask[b][1] = c->blk[b].mask[1];
+        cm.eta[b] = c->blk[b].eta;
+        cm.c_log2[b] = c->blk[b].c_log2;
+        cm.k_loc[b] = c->blk[b].k_loc;
+        cm.part[b] = c->blk[b].dPart.as<ef::d4>();
+        cm.eta_max = std::max(cm.eta_max, c->blk[b].eta);
+    }
+    cm.tol = c->opt.tol;
+    cm.p_floor = c->p_floor;
+    // FP32 error model: |d det| ~ K eta u32 |det| / |weakest pivot| with K = 2
+    cm.err_coef = fp64_only ? 0.0 : 2.0 * std::max(1, cm.eta_max) * std::ldexp(1.0, -24);
+
+    if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
+    const int64_t lu_launches_before = st.launches;
+    for (int b = 0; b < c->nblocks; ++b) {
+        ef::ExactBlockDev d = exact_block_dev(c, b);
+        if (fp64_only) {
+            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, nullptr, nullptr, nb, true, s, st));
+        } else if (d.eta <= ef::kMaxEtaThread) {
+            EF_CK(ef::launch_exact_lu_f32(d, d_bits, nb, s, st));
+        } else {
+            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, nullptr, nullptr, nb, false, s, st));
+        }
+    }
+    if (c->timed) EF_CK(cudaEventRecord(c->ev1, s));
+    c->stats.dominant_kernel_launches = st.launches - lu_launches_before;
+    c->stats.dominant_kernel_flops = flops;
+
+    const bool autofix = prec == EF_PREC_AUTO;
+    if (autofix) {
+        EF_CK(c->dList.ensure((size_t)nb * sizeof(int)));
+        EF_CK(c->dListCount.ensure(sizeof(int)));
+        EF_CK(cudaMemsetAsync(c->dListCount.p, 0, sizeof(int), s));
+    }
+    EF_CK(ef::launch_exact_combine(cm, d_bits, nb, nullptr, nullptr, d_out, d_err,
+                                   autofix ? c->dList.as<int>() : nullptr,
+                                   autofix ? c->dListCount.as<int>() : nullptr, s, st));
+    if (autofix) {
+        for (int b = 0; b < c->nblocks; ++b) {
+            ef::ExactBlockDev d = exact_block_dev(c, b);
+            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, c->dList.as<int>(), c->dListCount.as<int>(), nb, true, s,
+                                           st));
+        }
+        cm.err_coef = 0.0;
+        EF_CK(ef::launch_exact_combine(cm, d_bits, nb, c->dList.as<int>(), c->dListCount.as<int>(), d_out, d_err,
+                                       nullptr, nullptr, s, st));
+        c->last_fp64_list_pending = 1;
+    }
+    c->stats.kernel_launches = st.launches;
+    c->stats.executed_minor_lus = st.executed_lus;
+    return EF_OK;
+}
+
+int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uint64_t seed, uint64_t base,
+               double* d_out, double* d_se, cudaStream_t s) {
+    if (!c->approx_ok) return fail(EF_EUNSUPPORTED, c->approx_why);
+    if (t <= 0 || t > (int64_t)4294967296ll) return fail(EF_EINVAL, "n_traj must be in 1..2^32");
+    int rc = begin_call(c, s, 2);
+    if (rc) return rc;
+    const bool fp64 = c->opt.precision == EF_PREC_FP64;
+    ef::LaunchStats st;
+    c->stats.logical_branch_dets = nb * t;
+    if (nb == 0) return EF_OK;
+    ef::ApproxDev a{};
+    a.nblocks = c->nblocks;
+    a.k = (int)c->cps.size();
+    a.T = c->daT.as<uint32_t>();
+    a.qratio = c->daq.as<double>();
+    a.glayer = c->dalayer.as<uint8_t>();
+    a.gmodes = c->damodes.as<uint64_t>();
+    a.R0 = c->R0;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.index_base = base;
+    a.inactive0 = c->inactive[0];
+    a.inactive1 = c->inactive[1];
+    a.t = t;
+    a.traj_per_cta = 128 * 16;
+    a.n_chunks = (int)((t + a.traj_per_cta - 1) / a.traj_per_cta);
+    if (a.n_chunks > 65535) {
+        a.traj_per_cta = (int)((t + 65534) / 65535);
+        a.traj_per_cta = (a.traj_per_cta + 127) / 128 * 128;
+        a.n_chunks = (int)((t + a.traj_per_cta - 1) / a.traj_per_cta);
+    }
+    if (nb > 2147483647ll) return fail(EF_EUNSUPPORTED, "Raw Estimate: more than 2^31-1 bitstrings per call");
+    EF_CK(c->daPart.ensure((size_t)nb * a.n_chunks * 8 * sizeof(double)));
+    EF_CK(c->dCounters.ensure(4 * sizeof(unsigned long long)));
+    EF_CK(cudaMemsetAsync(c->dCounters.p, 0, 4 * sizeof(unsigned long long), s));
+    a.part = c->daPart.as<double>();
+    a.counters = c->dCounters.as<unsigned long long>();
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        a.blk[b].n = B.n;
+        a.blk[b].eta = B.eta;
+        a.blk[b].L = B.L;
+        a.blk[b].mask0 = B.mask[0];
+        a.blk[b].mask1 = B.mask[1];
+        a.blk[b].P = fp64 ? B.dP64.p : B.dP32.p;
+        a.blk[b].RC = fp64 ? B.dRC64.p : B.dRC32.p;
+        a.blk[b].cols = B.dCols.as<int>();
+    }
+    if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
+    EF_CK(ef::launch_approx(a, d_bits, nb, fp64, s, st));
+    if (c->timed) EF_CK(cudaEventRecord(c->ev1, s));
+    c->stats.dominant_kernel_launches = 1;
+    EF_CK(ef::launch_approx_finalize(a, nb, d_out, d_se, s, st));
+    c->stats.kernel_launches = st.launches;
+    return EF_OK;
+}
+
+template <typename F>
+int host_call(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, double* out2, F&& dev_call) {
+    if (!c->own_stream) EF_CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    cudaStream_t s = c->own_stream;
+    if (nb > 0) {
+        EF_CK(c->dBits.ensure((size_t)nb * 2 * sizeof(uint64_t)));
+        EF_CK(c->dOut.ensure((size_t)nb * sizeof(double)));
+        if (out2) EF_CK(c->dErr.ensure((size_t)nb * sizeof(double)));
+        EF_CK(cudaMemcpyAsync(c->dBits.p, bits, (size_t)nb * 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    }
+    int rc = dev_call(c->dBits.as<uint64_t>(), c->dOut.as<double>(), out2 ? c->dErr.as<double>() : nullptr, s);
+    if (rc) return rc;
+    if (nb > 0) {
+        EF_CK(cudaMemcpyAsync(out, c->dOut.p, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (out2) EF_CK(cudaMemcpyAsync(out2, c->dErr.p, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    EF_CK(cudaStreamSynchronize(s));
+    return EF_OK;
+}
+
+int check_bits_host(const ef_circuit* c, const uint64_t* bits, int64_t nb) {
+    uint64_t hi[2] = {0, 0};
+    if (c->n < 64) hi[0] = ~0ull << c->n, hi[1] = ~0ull;
+    else if (c->n < 128) hi[1] = ~0ull << (c->n - 64);
+    for (int64_t i = 0; i < nb; ++i)
+        if ((bits[2 * i] & hi[0]) || (bits[2 * i + 1] & hi[1]))
+            return fail(EF_EINVAL, "bitstring " + std::to_string(i) + " has a bit at or above n_modes");
+    return EF_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+int ef_version(void) { return 100; }
+
+const char* ef_last_error(void) { return g_err.c_str(); }
+
+int ef_circuit_create(int32_t n_modes, const uint64_t occupation[2], const ef_gate* gates, int64_t n_gates,
+                      const ef_options* opt, ef_circuit** out) {
+    if (!out) return fail(EF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!occupation) return fail(EF_EINVAL, "occupation is NULL");
+    if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(EF_EINVAL, "bad gate list");
+    if (n_modes < 1 || n_modes > ef::kMaxModes) return fail(EF_EINVAL, "n_modes must be in 1..128");
+    uint64_t hi[2] = {0, 0};
+    if (n_modes < 64) hi[0] = ~0ull << n_modes, hi[1] = ~0ull;
+    else if (n_modes < 128) hi[1] = ~0ull << (n_modes - 64);
+    if ((occupation[0] & hi[0]) || (occupation[1] & hi[1])) return fail(EF_EINVAL, "occupation has a bit at or above n_modes");
+    int rc = validate_gates(n_modes, gates, n_gates);
+    if (rc) return rc;
+    ef_circuit* c = new (std::nothrow) ef_circuit();
+    if (!c) return fail(EF_ENOMEM, "host allocation failed");
+    c->n = n_modes;
+    c->occ[0] = occupation[0];
+    c->occ[1] = occupation[1];
+    c->gates.assign(gates, gates + n_gates);
+    c->opt.precision = EF_PREC_AUTO;
+    c->opt.flags = 0;
+    c->opt.tol = 1e-5;
+    if (opt) {
+        c->opt = *opt;
+        if (c->opt.precision < 0 || c->opt.precision > 2) {
+            delete c;
+            return fail(EF_EINVAL, "bad precision");
+        }
+        if (!(c->opt.tol > 0)) c->opt.tol = 1e-5;
+    }
+    // the device is only needed by the probability calls; creation and the host
+    // preprocessing work without one
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        c->device = -1;
+        cudaGetLastError();
+    }
+    rc = prepare(c);
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return EF_OK;
+}
+
+int ef_circuit_destroy(ef_circuit* c) {
+    if (!c) return EF_OK;
+    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    delete c;
+    return EF_OK;
+}
+
+int ef_circuit_num_angles(const ef_circuit* c, int64_t* n) {
+    if (!c || !n) return fail(EF_EINVAL, "NULL argument");
+    int64_t k = 0;
+    for (const ef_gate& g : c->gates) k += g.kind == EF_GIVENS ? 2 : 1;
+    *n = k;
+    return EF_OK;
+}
+
+int ef_circuit_get_angles(const ef_circuit* c, double* angles, int64_t n) {
+    int64_t k;
+    int rc = ef_circuit_num_angles(c, &k);
+    if (rc) return rc;
+    if (n != k || (k > 0 && !angles)) return fail(EF_EINVAL, "angle count mismatch");
+    int64_t i = 0;
+    for (const ef_gate& g : c->gates) {
+        if (g.kind == EF_GIVENS) {
+            angles[i++] = g.theta;
+            angles[i++] = g.phi;
+        } else if (g.kind == EF_PHASE) {
+            angles[i++] = g.phi;
+        } else {
+            angles[i++] = g.theta;
+        }
+    }
+    return EF_OK;
+}
+
+int ef_circuit_set_angles(ef_circuit* c, const double* angles, int64_t n) {
+    int64_t k;
+    int rc = ef_circuit_num_angles(c, &k);
+    if (rc) return rc;
+    if (n != k || (k > 0 && !angles)) return fail(EF_EINVAL, "angle count mismatch");
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(angles[i])) return fail(EF_EINVAL, "non-finite angle");
+    if (c->last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
+    int64_t i = 0;
+    for (ef_gate& g : c->gates) {
+        if (g.kind == EF_GIVENS) {
+            g.theta = angles[i++];
+            g.phi = angles[i++];
+        } else if (g.kind == EF_PHASE) {
+            g.phi = angles[i++];
+        } else {
+            g.theta = angles[i++];
+        }
+    }
+    return prepare(c);
+}
+
+int ef_circuit_extent(const ef_circuit* c, double* xi) {
+    if (!c || !xi) return fail(EF_EINVAL, "NULL argument");
+    *xi = c->xi;
+    return EF_OK;
+}
+
+int ef_circuit_set_precision(ef_circuit* c, int32_t precision, double tol) {
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    if (precision < 0 || precision > 2) return fail(EF_EINVAL, "bad precision");
+    if (c->last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
+    c->opt.precision = precision;
+    if (tol > 0) c->opt.tol = tol;
+    return EF_OK;
+}
+
+int ef_prob_exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out, double* d_err_out,
+                      void* stream) {
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    if (nb < 0 || (nb > 0 && (!d_bits || !d_out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
+    if (nb > 2147483647ll) return fail(EF_EUNSUPPORTED, "more than 2^31-1 bitstrings per call");
+    return exact_dev(c, d_bits, nb, d_out, d_err_out, (cudaStream_t)stream);
+}
+
+int ef_prob_exact(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, double* err_out) {
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    if (nb < 0 || (nb > 0 && (!bits || !out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
+    int rc = check_bits_host(c, bits, nb);
+    if (rc) return rc;
+    return host_call(c, bits, nb, out, err_out, [&](const uint64_t* db, double* dout, double* derr, cudaStream_t s) {
+        return ef_prob_exact_dev(c, db, nb, dout, derr, s);
+    });
+}
+
+int ef_prob_approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t n_traj, uint64_t seed,
+                       uint64_t index_base, double* d_out, double* d_stderr_out, void* stream) {
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    if (nb < 0 || (nb > 0 && (!d_bits || !d_out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
+    return approx_dev(c, d_bits, nb, n_traj, seed, index_base, d_out, d_stderr_out, (cudaStream_t)stream);
+}
+
+int ef_prob_approx(ef_circuit* c, const uint64_t* bits, int64_t nb, int64_t n_traj, uint64_t seed,
+                   uint64_t index_base, double* out, double* stderr_out) {
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    if (nb < 0 || (nb > 0 && (!bits || !out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
+    int rc = check_bits_host(c, bits, nb);
+    if (rc) return rc;
+    return host_call(c, bits, nb, out, stderr_out, [&](const uint64_t* db, double* dout, double* dse, cudaStream_t s) {
+        return ef_prob_approx_dev(c, db, nb, n_traj, seed, index_base, dout, dse, s);
+    });
+}
+
+int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_grad_p, double* d_out_p,
+                     double* d_grad_angles, void* stream) {
+    (void)d_bits; (void)nb; (void)d_grad_p; (void)d_out_p; (void)d_grad_angles; (void)stream;
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    return fail(EF_EUNSUPPORTED, "ef_prob_grad: adjoint path not built yet");
+}
+
+int ef_prob_grad(ef_circuit* c, const uint64_t* bits, int64_t nb, const double* grad_p, double* out_p,
+                 double* grad_angles) {
+    (void)bits; (void)nb; (void)grad_p; (void)out_p; (void)grad_angles;
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    return fail(EF_EUNSUPPORTED, "ef_prob_grad: adjoint path not built yet");
+}
+
+int ef_circuit_get_stats(ef_circuit* c, ef_stats* st) {
+    if (!c || !st) return fail(EF_EINVAL, "NULL argument");
+    if (c->last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
+    if (c->timed && c->ev0 && c->stats.dominant_kernel_launches > 0) {
+        float ms = 0.f;
+        EF_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        c->stats.dominant_kernel_ms = ms;
+    }
+    if (c->last_mode == 1 && c->last_fp64_list_pending) {
+        int cnt = 0;
+        EF_CK(cudaMemcpy(&cnt, c->dListCount.p, sizeof(int), cudaMemcpyDeviceToHost));
+        c->stats.fp64_recomputed = cnt;
+        c->stats.executed_minor_lus += (int64_t)cnt * c->last_sub_total;
+        c->last_fp64_list_pending = 0;
+    }
+    if (c->last_mode == 2 && c->dCounters.p) {
+        unsigned long long h[4] = {0, 0, 0, 0};
+        EF_CK(cudaMemcpy(h, c->dCounters.p, sizeof(h), cudaMemcpyDeviceToHost));
+        c->stats.sampled_flips = (int64_t)h[0];
+        c->stats.executed_minor_lus = (int64_t)h[1];
+    }
+    *st = c->stats;
+    return EF_OK;
+}
+
+}  // extern "C"

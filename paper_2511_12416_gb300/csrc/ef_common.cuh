@@ -1,0 +1,263 @@
+// Device helpers: complex arithmetic on float2/double2, the Philox4x32-10
+// generator and the two small-matrix LU determinant routines used by the
+// Exact and Raw Estimate kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ef {
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+template <typename R> using cplx_t = typename V2<R>::T;
+
+__host__ __device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
+__host__ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
+
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+    T r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// a - l * p
+template <typename T> __device__ __forceinline__ T cfms(T a, T l, T p) {
+    T r;
+    r.x = fma(-l.x, p.x, fma(l.y, p.y, a.x));
+    r.y = fma(-l.x, p.y, fma(-l.y, p.x, a.y));
+    return r;
+}
+// a + l * p
+template <typename T> __device__ __forceinline__ T cfma(T a, T l, T p) {
+    T r;
+    r.x = fma(l.x, p.x, fma(-l.y, p.y, a.x));
+    r.y = fma(l.x, p.y, fma(l.y, p.x, a.y));
+    return r;
+}
+template <typename T> __device__ __forceinline__ auto abs2(T a) -> decltype(a.x) {
+    return fma(a.x, a.x, a.y * a.y);
+}
+
+__device__ __forceinline__ float recip(float m) { return __frcp_rn(m); }
+__device__ __forceinline__ double recip(double m) { return 1.0 / m; }
+
+// multiply by i^ph (ph in 0..3)
+__device__ __forceinline__ double2 times_i_pow(double2 a, int ph) {
+    switch (ph & 3) {
+        case 0: return a;
+        case 1: return make_double2(-a.y, a.x);
+        case 2: return make_double2(-a.x, -a.y);
+        default: return make_double2(a.y, -a.x);
+    }
+}
+
+// Swap a and b when msk is all ones (no-op when it is zero).
+__device__ __forceinline__ void swap_if(float2& a, float2& b, uint32_t msk) {
+    const uint32_t dx = (__float_as_uint(a.x) ^ __float_as_uint(b.x)) & msk;
+    const uint32_t dy = (__float_as_uint(a.y) ^ __float_as_uint(b.y)) & msk;
+    a.x = __uint_as_float(__float_as_uint(a.x) ^ dx);
+    a.y = __uint_as_float(__float_as_uint(a.y) ^ dy);
+    b.x = __uint_as_float(__float_as_uint(b.x) ^ dx);
+    b.y = __uint_as_float(__float_as_uint(b.y) ^ dy);
+}
+__device__ __forceinline__ void swap_if(double2& a, double2& b, uint32_t msk) {
+    const uint64_t m = (uint64_t)msk | ((uint64_t)msk << 32);
+    const uint64_t dx = (__double_as_longlong(a.x) ^ __double_as_longlong(b.x)) & m;
+    const uint64_t dy = (__double_as_longlong(a.y) ^ __double_as_longlong(b.y)) & m;
+    a.x = __longlong_as_double(__double_as_longlong(a.x) ^ dx);
+    a.y = __longlong_as_double(__double_as_longlong(a.y) ^ dy);
+    b.x = __longlong_as_double(__double_as_longlong(b.x) ^ dx);
+    b.y = __longlong_as_double(__double_as_longlong(b.y) ^ dy);
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al., SC'11: ten rounds; each multiplies counter words 0 and 2 by
+// fixed odd constants, keeps the high and low product halves and mixes the
+// high halves with the other words and the key; the key advances by two Weyl
+// constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------- bitstrings
+// Local row indices (ascending) of the set bits of (w0, w1) inside a block
+// given by its global mode mask. Returns false unless there are exactly N.
+template <int N>
+__device__ __forceinline__ bool decode_rows(uint64_t w0, uint64_t w1, uint64_t m0, uint64_t m1,
+                                            int (&rows)[N]) {
+    w0 &= m0;
+    w1 &= m1;
+    const int base1 = __popcll(m0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        int r = -1;
+        if (w0) {
+            const int m = __ffsll((long long)w0) - 1;
+            w0 &= w0 - 1;
+            r = __popcll(m0 & ((1ull << m) - 1ull));
+        } else if (w1) {
+            const int m = __ffsll((long long)w1) - 1;
+            w1 &= w1 - 1;
+            r = base1 + __popcll(m1 & ((1ull << m) - 1ull));
+        }
+        rows[i] = r;
+    }
+    bool ok = (w0 == 0) && (w1 == 0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) ok = ok && rows[i] >= 0;
+    return ok;
+}
+
+// The local row index of the r-th set bit (r < popcount) of (w0,w1) & mask,
+// or -1; also returns the popcount through cnt.
+__device__ __forceinline__ int nth_row(uint64_t w0, uint64_t w1, uint64_t m0, uint64_t m1, int r,
+                                       int& cnt) {
+    w0 &= m0;
+    w1 &= m1;
+    const int c0 = __popcll(w0);
+    cnt = c0 + __popcll(w1);
+    if (r < 0 || r >= cnt) return -1;
+    uint64_t w = (r < c0) ? w0 : w1;
+    int rr = (r < c0) ? r : r - c0;
+    for (int i = 0; i < rr; ++i) w &= w - 1;
+    const int m = __ffsll((long long)w) - 1;
+    if (r < c0) return __popcll(m0 & ((1ull << m) - 1ull));
+    return __popcll(m0) + __popcll(m1 & ((1ull << m) - 1ull));
+}
+
+// ---------------------------------------------------------------- LU determinants
+// Thread-per-minor LU with partial pivoting (largest |a|^2 in the column,
+// lowest current row on ties) on an N x N matrix in registers. Returns the
+// determinant and, through esq, the squared magnitude of the product of all
+// pivots but the smallest (the smallest replaced by 1 when it is above 1):
+// the size of the determinant's sensitivity to its weakest pivot, used by the
+// FP32 error estimate. The elimination steps are a compile-time recursion so
+// every matrix index is a constant and the matrix stays in registers.
+template <typename R, int N, int K>
+__device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], cplx_t<R>& d, bool& odd, R& minsq, R& prodsq) {
+    if constexpr (K < N) {
+        using T = cplx_t<R>;
+        R best = abs2(A[K][K]);
+        int p = K;
+#pragma unroll
+        for (int i = K + 1; i < N; ++i) {
+            const R m = abs2(A[i][K]);
+            const bool gt = m > best;
+            best = gt ? m : best;
+            p = gt ? i : p;
+        }
+        odd ^= (p != K);
+#pragma unroll
+        for (int i = K + 1; i < N; ++i) {
+            // branch-free swap of rows K and i when i is the pivot row, done on
+            // the bit patterns so that the rows stay in registers
+            const uint32_t msk = 0u - (uint32_t)(p == i);
+#pragma unroll
+            for (int j = K; j < N; ++j) swap_if(A[K][j], A[i][j], msk);
+        }
+        const T piv = A[K][K];
+        const bool lower = best < minsq;
+        prodsq *= lower ? minsq : best;
+        minsq = lower ? best : minsq;
+        d = cmul(d, piv);
+        const R inv = best > R(0) ? recip(best) : R(0);
+        const T ip = mk(piv.x * inv, -piv.y * inv);
+#pragma unroll
+        for (int i = K + 1; i < N; ++i) {
+            const T l = cmul(A[i][K], ip);
+#pragma unroll
+            for (int j = K + 1; j < N; ++j) A[i][j] = cfms(A[i][j], l, A[K][j]);
+        }
+        lu_step<R, N, K + 1>(A, d, odd, minsq, prodsq);
+    }
+}
+
+template <typename R, int N>
+__device__ __forceinline__ cplx_t<R> lu_det_regs(cplx_t<R> (&A)[N][N], R& esq) {
+    using T = cplx_t<R>;
+    T d = mk(R(1), R(0));
+    bool odd = false;
+    R minsq = R(1), prodsq = R(1);
+    lu_step<R, N, 0>(A, d, odd, minsq, prodsq);
+    esq = prodsq;
+    return odd ? mk(-d.x, -d.y) : d;
+}
+
+// Warp-row LU: a group of G lanes (G a power of two, 1 < G <= 32) holds one
+// eta x eta minor, lane r of the group owning row r (rows >= eta are padding).
+// The rows never move: at step k the group finds the pivot row p (largest
+// |a_rk|^2 among rows not yet used, lowest r on ties) by shuffles, broadcasts
+// its remaining entries and every other unused row eliminates against it.
+// The permutation's sign is the parity of the number of unused rows below p
+// at each step. All 32 lanes of the warp must call this with the same eta.
+template <typename R, int G>
+__device__ __forceinline__ cplx_t<R> lu_det_rows(cplx_t<R> (&row)[G], int r, int eta, R& esq) {
+    using T = cplx_t<R>;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int gbase = lane & ~(G - 1);
+    const unsigned gmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    bool done = (r >= eta);
+    T d = mk(R(1), R(0));
+    int inv = 0;
+    R minsq = R(1), prodsq = R(1);
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        if (k >= eta) break;
+        R mag = done ? R(-1) : abs2(row[k]);
+        int idx = r;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            const R om = __shfl_xor_sync(full, mag, off, G);
+            const int oi = __shfl_xor_sync(full, idx, off, G);
+            if (om > mag || (om == mag && oi < idx)) {
+                mag = om;
+                idx = oi;
+            }
+        }
+        const int p = idx;
+        const unsigned act = (__ballot_sync(full, !done) >> gbase) & gmask;
+        inv += __popc(act & ((1u << p) - 1u));
+        T piv;
+        piv.x = __shfl_sync(full, row[k].x, p, G);
+        piv.y = __shfl_sync(full, row[k].y, p, G);
+        const R best = mag;
+        if (best < minsq) {
+            prodsq *= minsq;
+            minsq = best;
+        } else {
+            prodsq *= best;
+        }
+        d = cmul(d, piv);
+        const R invm = best > R(0) ? recip(best) : R(0);
+        const T ip = mk(piv.x * invm, -piv.y * invm);
+        const bool upd = !done && (r != p);
+        const T l = cmul(row[k], ip);
+#pragma unroll
+        for (int j = k + 1; j < G; ++j) {
+            if (j >= eta) break;
+            T pj;
+            pj.x = __shfl_sync(full, row[j].x, p, G);
+            pj.y = __shfl_sync(full, row[j].y, p, G);
+            if (upd) row[j] = cfms(row[j], l, pj);
+        }
+        if (r == p) done = true;
+    }
+    esq = prodsq;
+    return (inv & 1) ? mk(-d.x, -d.y) : d;
+}
+
+}  // namespace ef

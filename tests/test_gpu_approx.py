@@ -1,0 +1,114 @@
+"""GPU parity of the Raw Estimate (Eqs. 10-12) against the FP64 CPU oracle.
+
+Both sides draw the same trajectories (Philox4x32-10 keyed by seed, global
+bitstring index and trajectory number, integer thresholds), so the estimator
+itself is a deterministic function compared element by element:
+|p_gpu - p_oracle| <= 1e-10 * max(p, p_floor) on the FP64 path and 1e-5 on
+the FP32-minor path; the total number of sampled flips must match exactly."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def run_approx(lib, c, bits, t, seed, precision, index_base=0):
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=precision)
+    try:
+        p, se = lib.ef_prob_approx(h, bits, t, seed=seed, index_base=index_base)
+        st = lib.ef_circuit_get_stats(h)
+    finally:
+        lib.ef_circuit_destroy(h)
+    return p, se, st
+
+
+CASES = [
+    ("config1", lambda: W.config1(), 3000),
+    ("random-n10-eta4-k7", lambda: (W.random_fig4_circuit(10, 4, 7, 3, seed=31, angle_std=1.2),
+                                    W.sector_bitstrings_all(10, 4)[:60]), 1000),
+    ("lucj-12q", lambda: (W.lucj_circuit(6, 3, 3, 1, n_onsite=6, n_same=3, angle_sampler=W.normal_var(0.1),
+                                         seed=7), W.spin_sector_bitstrings_all(6, 3, 3)[:50]), 2000),
+    ("lucj-16q-3layer", lambda: (W.lucj_circuit(8, 3, 2, 3, n_onsite=4, n_same=2, angle_sampler=W.normal_var(0.4),
+                                                seed=12), W.spin_sector_bitstrings(8, 3, 2, 40, np.random.default_rng(2))),
+     2500),
+]
+
+
+@pytest.mark.parametrize("name,maker,t", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_approx_matches_oracle_same_trajectories(lib, name, maker, t, prec):
+    c, bits = maker()
+    seed = 0x1234_5678_9ABC
+    p_ref, se_ref, _, flips_ref = O.raw_estimate(c, bits, t=t, seed=seed, return_details=True)
+    precision = lib.EF_PREC_FP64 if prec == "fp64" else lib.EF_PREC_FP32_MINOR
+    p, se, st = run_approx(lib, c, bits, t, seed, precision)
+    n = c.n_modes
+    floor = 1e-6 / math.comb(n, len(c.occupied_modes()))
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(p - p_ref) / np.maximum(p_ref, floor)) <= tol
+    assert np.max(np.abs(se - se_ref) / np.maximum(se_ref, floor)) <= (1e-8 if prec == "fp64" else 1e-3)
+    assert st["sampled_flips"] == flips_ref
+    assert st["logical_branch_dets"] == len(bits) * t
+
+
+def test_approx_global_index_and_subsets(lib):
+    c, bits = W.config1()
+    p_all, se_all, _ = run_approx(lib, c, bits, 500, 7, lib.EF_PREC_FP64)
+    p_sub, se_sub, _ = run_approx(lib, c, bits[30:45], 500, 7, lib.EF_PREC_FP64, index_base=30)
+    assert np.array_equal(p_sub, p_all[30:45]) and np.array_equal(se_sub, se_all[30:45])
+
+
+def test_approx_zero_angles_is_exact(lib):
+    c, bits = W.config1()
+    recs = [(int(g["kind"]), int(g["p"]), int(g["q"]), 0.0 if int(g["kind"]) == W.CPHASE else float(g["theta"]),
+             float(g["phi"])) for g in c.gates]
+    c0 = W.Circuit(8, c.occupation, W.make_gates(recs))
+    p, se, st = run_approx(lib, c0, bits, 333, 1, lib.EF_PREC_FP64)
+    assert np.max(np.abs(p - O.exact_probabilities(c0, bits))) < 1e-15
+    assert np.all(se < 1e-14) and st["sampled_flips"] == 0
+
+
+def test_approx_edge_cases(lib):
+    c, bits = W.config1()
+    bad = np.array([W.modes_to_bits([0, 1]), W.modes_to_bits([0, 1, 2, 3, 4])], dtype=np.uint64)
+    p, se, _ = run_approx(lib, c, bad, 100, 0, lib.EF_PREC_FP32_MINOR)
+    assert np.all(p == 0) and np.all(se == 0)
+    p, se, _ = run_approx(lib, c, bits[:3], 1, 0, lib.EF_PREC_FP64)
+    assert np.all(se == 0)
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates)
+    try:
+        with pytest.raises(lib.ExtraFermError):
+            lib.ef_prob_approx(h, bits[:3], 0)
+    finally:
+        lib.ef_circuit_destroy(h)
+
+
+def test_approx_unbiased_against_exact(lib):
+    """Many independent seeds: the mean of alpha-estimates' |.|^2 follows the
+    exact bias formula E[p_hat] = p + (E|Y|^2 - p)/t."""
+    c = W.random_fig4_circuit(6, 3, 5, 2, seed=31, angle_std=1.5)
+    b = W.sector_bitstrings_all(6, 3)[7:8]
+    alpha, m2 = O.expected_second_moment(c, b[0])
+    p = abs(alpha) ** 2
+    t = 64
+    bits = np.repeat(b, 2000, axis=0)  # each row has its own global index -> independent trajectories
+    ph, _, _ = run_approx(lib, c, bits, t, 99, lib.EF_PREC_FP64)
+    z = (ph.mean() - (p + (m2 - p) / t)) / (ph.std(ddof=1) / math.sqrt(len(ph)))
+    assert abs(z) < 4.0
+
+
+def test_approx_config3_full_trajectory_count_sampled(lib):
+    """Config 3 (52 modes, k=152, t = ceil(extent/eps^2)) at full t on 256
+    bitstrings; the oracle checks two of them."""
+    c, bits = W.config3(256)
+    t = W.config3_trajectories(O.extent(c.gates))
+    p, se, st = run_approx(lib, c, bits, t, 0, lib.EF_PREC_FP32_MINOR)
+    idx = [0, 201]
+    p_ref, se_ref = O.raw_estimate(c, bits[idx], t=t, seed=0, b_indices=idx)
+    floor = 1e-6 / (math.comb(26, 5) ** 2)
+    assert np.max(np.abs(p[idx] - p_ref) / np.maximum(p_ref, floor)) <= 1e-5
+    assert np.all(np.isfinite(p)) and np.all(p >= 0)
