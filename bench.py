@@ -323,9 +323,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "fp64", "fp32"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nb", type=int, default=NB, help="bitstrings per GPU (profiling runs use fewer)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    global NB
+    NB = args.nb
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -95,7 +95,8 @@ typedef struct {
     int32_t precision;         /* ef_precision; default EF_PREC_AUTO */
     int32_t flags;             /* EF_FLAG_* */
     double tol;                /* relative-error target of EF_PREC_AUTO, default 1e-5 */
-    int32_t tile_override[4];  /* 0 = automatic; [0] = FP32 Exact sub-branches per chunk (log2) */
+    int32_t tile_override[4];  /* 0 = automatic; [0] = FP32 Exact sub-branches per chunk (log2);
+                                  [1] = constant K of the FP32 error estimate in tenths (default 30) */
 } ef_options;
 
 typedef struct {

@@ -168,6 +168,7 @@ struct ef_circuit {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
     cudaStream_t last_stream = nullptr;
+    bool has_last_stream = false;  // the legacy default stream is a null handle
     ef_stats stats{};
     int64_t last_fp64_list_pending = 0;  // 1 if the fp64 list count must be read back
     int64_t last_sub_total = 0;          // sum over blocks of 2^k_B (for executed-LU accounting)
@@ -575,8 +576,9 @@ double lu_flops(int eta) {
 }
 
 int begin_call(ef_circuit* c, cudaStream_t s, int mode) {
-    if (c->last_stream && c->last_stream != s) EF_CK(cudaStreamSynchronize(c->last_stream));
+    if (c->has_last_stream && c->last_stream != s) EF_CK(cudaStreamSynchronize(c->last_stream));
     c->last_stream = s;
+    c->has_last_stream = true;
     c->stats = ef_stats{};
     c->last_mode = mode;
     c->last_fp64_list_pending = 0;
@@ -662,8 +664,12 @@ int exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out, 
     }
     cm.tol = c->opt.tol;
     cm.p_floor = c->p_floor;
-    // FP32 error model: |d det| ~ K eta u32 |det| / |weakest pivot| with K = 2
-    cm.err_coef = fp64_only ? 0.0 : 2.0 * std::max(1, cm.eta_max) * std::ldexp(1.0, -24);
+    // FP32 error model: |d det|^2 ~ (K u32)^2 (|det|^2 er2 + zabs2) per minor,
+    // independent between minors (combined in quadrature). K = 3 covers the
+    // largest observed actual/estimated ratio (2.3 at K = 1) with margin;
+    // ef_options.tile_override[1] > 0 sets K in tenths.
+    const double K = c->opt.tile_override[1] > 0 ? 0.1 * c->opt.tile_override[1] : 3.0;
+    cm.err_coef = fp64_only ? 0.0 : K * std::ldexp(1.0, -24);
 
     if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
     const int64_t lu_launches_before = st.launches;
@@ -850,7 +856,7 @@ int ef_circuit_create(int32_t n_modes, const uint64_t occupation[2], const ef_ga
 
 int ef_circuit_destroy(ef_circuit* c) {
     if (!c) return EF_OK;
-    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    if (c->has_last_stream) cudaStreamSynchronize(c->last_stream);
     delete c;
     return EF_OK;
 }
@@ -889,7 +895,7 @@ int ef_circuit_set_angles(ef_circuit* c, const double* angles, int64_t n) {
     if (n != k || (k > 0 && !angles)) return fail(EF_EINVAL, "angle count mismatch");
     for (int64_t i = 0; i < n; ++i)
         if (!std::isfinite(angles[i])) return fail(EF_EINVAL, "non-finite angle");
-    if (c->last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
+    if (c->has_last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
     int64_t i = 0;
     for (ef_gate& g : c->gates) {
         if (g.kind == EF_GIVENS) {
@@ -913,7 +919,7 @@ int ef_circuit_extent(const ef_circuit* c, double* xi) {
 int ef_circuit_set_precision(ef_circuit* c, int32_t precision, double tol) {
     if (!c) return fail(EF_EINVAL, "NULL circuit");
     if (precision < 0 || precision > 2) return fail(EF_EINVAL, "bad precision");
-    if (c->last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
+    if (c->has_last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
     c->opt.precision = precision;
     if (tol > 0) c->opt.tol = tol;
     return EF_OK;
@@ -971,7 +977,7 @@ int ef_prob_grad(ef_circuit* c, const uint64_t* bits, int64_t nb, const double* 
 
 int ef_circuit_get_stats(ef_circuit* c, ef_stats* st) {
     if (!c || !st) return fail(EF_EINVAL, "NULL argument");
-    if (c->last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
+    if (c->has_last_stream) EF_CK(cudaStreamSynchronize(c->last_stream));
     if (c->timed && c->ev0 && c->stats.dominant_kernel_launches > 0) {
         float ms = 0.f;
         EF_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));

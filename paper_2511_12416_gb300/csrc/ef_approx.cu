@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(128) k_approx(ApproxDev A, const uint64_t* __r
         for (int i = 0; i < ETA; ++i)
 #pragma unroll
             for (int j = 0; j < ETA; ++j) M[i][j] = sA0[B][i * ETA + j];
-        R esq;
-        det0[B] = lu_det_regs<R, ETA>(M, esq);
+        R er2, zabs2;
+        det0[B] = lu_det_regs<R, ETA>(M, er2, zabs2);
         const double dr = (double)det0[B].x, di = (double)det0[B].y;
         const double nr = y0r * dr - y0i * di;
         y0i = y0r * di + y0i * dr;
@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(128) k_approx(ApproxDev A, const uint64_t* __r
                     if (!((lflag[B] >> (l - 1)) & 1u)) continue;
                     uint64_t Nl = N[B][l - 1];
                     const bool store = (lflag[B] & ((1u << (l - 1)) - 1u)) != 0;
+                    const int nabove = nst;  // columns of the layers above l only
                     while (Nl) {
                         const int i = __ffsll((long long)Nl) - 1;
                         Nl &= Nl - 1;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(128) k_approx(ApproxDev A, const uint64_t* __r
                         const T* left = sLeft[B] + (size_t)(l - 1) * ETA * n;
 #pragma unroll
                         for (int r = 0; r < ETA; ++r) h[r] = left[r * n + i];
-                        for (int st = 0; st < nst; ++st) {
+                        for (int st = 0; st < nabove; ++st) {
                             const int ls = htag[st] >> 8, is = htag[st] & 255;
                             const T mid = P[(size_t)tri(ls - 1, l) * n * n + (size_t)is * n + i];
 #pragma unroll
@@ -203,8 +204,8 @@ __global__ void __launch_bounds__(128) k_approx(ApproxDev A, const uint64_t* __r
                         }
                     }
                 }
-                R esq;
-                det = lu_det_regs<R, ETA>(M, esq);
+                R er2, zabs2;
+                det = lu_det_regs<R, ETA>(M, er2, zabs2);
                 ++nlu;
             }
             const double xr = (double)det.x, xi = (double)det.y;

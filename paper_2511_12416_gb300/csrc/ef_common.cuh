@@ -140,14 +140,20 @@ __device__ __forceinline__ int nth_row(uint64_t w0, uint64_t w1, uint64_t m0, ui
 
 // ---------------------------------------------------------------- LU determinants
 // Thread-per-minor LU with partial pivoting (largest |a|^2 in the column,
-// lowest current row on ties) on an N x N matrix in registers. Returns the
-// determinant and, through esq, the squared magnitude of the product of all
-// pivots but the smallest (the smallest replaced by 1 when it is above 1):
-// the size of the determinant's sensitivity to its weakest pivot, used by the
-// FP32 error estimate. The elimination steps are a compile-time recursion so
-// every matrix index is a constant and the matrix stays in registers.
+// lowest current row on ties) on an N x N matrix in registers.
+//
+// Besides the determinant it returns a rounding-error proxy for the FP32
+// path. Pivot u_kk is formed by k+1 rounded updates of entries no larger than
+// the original column's largest entry c_k, so its relative error is about
+// sqrt(k+1) u c_k / |u_kk|; the determinant's relative error squared is then
+// er2 = sum_k (k+1) c_k^2 / |u_kk|^2 (in units of u^2). A pivot that is
+// exactly zero leaves det = 0 with an absolute error of about
+// sqrt(k+1) u c_k prod_{j != k} |u_jj|; zabs2 is the square of that (0 when no
+// pivot vanished). The elimination steps are a compile-time recursion so every
+// matrix index is a constant and the matrix stays in registers.
 template <typename R, int N, int K>
-__device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], cplx_t<R>& d, bool& odd, R& minsq, R& prodsq) {
+__device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], const R (&cm2)[N], cplx_t<R>& d, bool& odd,
+                                        R& er2, R& pz, R& zc, int& nzero) {
     if constexpr (K < N) {
         using T = cplx_t<R>;
         R best = abs2(A[K][K]);
@@ -169,11 +175,13 @@ __device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], cplx_t<R>& d, bool
             for (int j = K; j < N; ++j) swap_if(A[K][j], A[i][j], msk);
         }
         const T piv = A[K][K];
-        const bool lower = best < minsq;
-        prodsq *= lower ? minsq : best;
-        minsq = lower ? best : minsq;
         d = cmul(d, piv);
-        const R inv = best > R(0) ? recip(best) : R(0);
+        const bool nz = best > R(0);
+        const R inv = nz ? recip(best) : R(0);
+        er2 = fma(R(K + 1) * cm2[K], inv, er2);
+        pz *= nz ? best : R(1);
+        zc = nz ? zc : R(K + 1) * cm2[K];
+        nzero += nz ? 0 : 1;
         const T ip = mk(piv.x * inv, -piv.y * inv);
 #pragma unroll
         for (int i = K + 1; i < N; ++i) {
@@ -181,18 +189,28 @@ __device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], cplx_t<R>& d, bool
 #pragma unroll
             for (int j = K + 1; j < N; ++j) A[i][j] = cfms(A[i][j], l, A[K][j]);
         }
-        lu_step<R, N, K + 1>(A, d, odd, minsq, prodsq);
+        lu_step<R, N, K + 1>(A, cm2, d, odd, er2, pz, zc, nzero);
     }
 }
 
 template <typename R, int N>
-__device__ __forceinline__ cplx_t<R> lu_det_regs(cplx_t<R> (&A)[N][N], R& esq) {
+__device__ __forceinline__ cplx_t<R> lu_det_regs(cplx_t<R> (&A)[N][N], R& er2, R& zabs2) {
     using T = cplx_t<R>;
+    R cm2[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        R m = abs2(A[0][j]);
+#pragma unroll
+        for (int i = 1; i < N; ++i) m = fmax(m, abs2(A[i][j]));
+        cm2[j] = m;
+    }
     T d = mk(R(1), R(0));
     bool odd = false;
-    R minsq = R(1), prodsq = R(1);
-    lu_step<R, N, 0>(A, d, odd, minsq, prodsq);
-    esq = prodsq;
+    R pz = R(1), zc = R(0);
+    int nzero = 0;
+    er2 = R(0);
+    lu_step<R, N, 0>(A, cm2, d, odd, er2, pz, zc, nzero);
+    zabs2 = (nzero == 1) ? zc * pz : R(0);
     return odd ? mk(-d.x, -d.y) : d;
 }
 
@@ -203,8 +221,9 @@ __device__ __forceinline__ cplx_t<R> lu_det_regs(cplx_t<R> (&A)[N][N], R& esq) {
 // its remaining entries and every other unused row eliminates against it.
 // The permutation's sign is the parity of the number of unused rows below p
 // at each step. All 32 lanes of the warp must call this with the same eta.
+// er2 and zabs2 are the rounding-error proxies of lu_det_regs.
 template <typename R, int G>
-__device__ __forceinline__ cplx_t<R> lu_det_rows(cplx_t<R> (&row)[G], int r, int eta, R& esq) {
+__device__ __forceinline__ cplx_t<R> lu_det_rows(cplx_t<R> (&row)[G], int r, int eta, R& er2, R& zabs2) {
     using T = cplx_t<R>;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -213,10 +232,22 @@ __device__ __forceinline__ cplx_t<R> lu_det_rows(cplx_t<R> (&row)[G], int r, int
     bool done = (r >= eta);
     T d = mk(R(1), R(0));
     int inv = 0;
-    R minsq = R(1), prodsq = R(1);
+    R pz = R(1), zc = R(0);
+    int nzero = 0;
+    er2 = R(0);
+    // largest |entry|^2 of every original column
+    R cm2[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        R cm = (done || j >= eta) ? R(0) : abs2(row[j]);
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) cm = fmax(cm, __shfl_xor_sync(full, cm, off, G));
+        cm2[j] = cm;
+    }
 #pragma unroll
     for (int k = 0; k < G; ++k) {
         if (k >= eta) break;
+        const R cm = cm2[k];
         R mag = done ? R(-1) : abs2(row[k]);
         int idx = r;
 #pragma unroll
@@ -235,14 +266,13 @@ __device__ __forceinline__ cplx_t<R> lu_det_rows(cplx_t<R> (&row)[G], int r, int
         piv.x = __shfl_sync(full, row[k].x, p, G);
         piv.y = __shfl_sync(full, row[k].y, p, G);
         const R best = mag;
-        if (best < minsq) {
-            prodsq *= minsq;
-            minsq = best;
-        } else {
-            prodsq *= best;
-        }
         d = cmul(d, piv);
-        const R invm = best > R(0) ? recip(best) : R(0);
+        const bool nz = best > R(0);
+        const R invm = nz ? recip(best) : R(0);
+        er2 = fma(R(k + 1) * cm, invm, er2);
+        pz *= nz ? best : R(1);
+        zc = nz ? zc : R(k + 1) * cm;
+        nzero += nz ? 0 : 1;
         const T ip = mk(piv.x * invm, -piv.y * invm);
         const bool upd = !done && (r != p);
         const T l = cmul(row[k], ip);
@@ -256,7 +286,7 @@ __device__ __forceinline__ cplx_t<R> lu_det_rows(cplx_t<R> (&row)[G], int r, int
         }
         if (r == p) done = true;
     }
-    esq = prodsq;
+    zabs2 = (nzero == 1) ? zc * pz : R(0);
     return (inv & 1) ? mk(-d.x, -d.y) : d;
 }
 

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
         d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
         if (ok) {
             double ar = 0.0, ai = 0.0;
-            float ssum = 0.f, esum = 0.f;
+            double ssum = 0.0, esum = 0.0;
             for (int t = 0; t < Y; ++t) {
                 const float2* Mt = smM + (size_t)t * n * S;
                 float2 A[ETA][ETA];
@@ -121,19 +121,20 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
 #pragma unroll
                     for (int j = 0; j < ETA; ++j) A[i][j] = rp[j];
                 }
-                float esq;
-                const float2 det = lu_det_regs<float, ETA>(A, esq);
+                float er2, zabs2;
+                const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
                 const uint32_t y = (uint32_t)chunk * (uint32_t)Y + (uint32_t)t;
                 const uint32_t yl = y & locmask;
                 const double wr = B.WLlo[yl & lomask] * B.WLhi[yl >> B.lobits];
                 const double2 wd = times_i_pow(make_double2(wr * (double)det.x, wr * (double)det.y), __popc(yl));
                 ar += wd.x;
                 ai += wd.y;
-                const float aw = fabsf((float)wr);
-                ssum = fmaf(aw, sqrtf(abs2(det)), ssum);
-                esum = fmaf(aw, sqrtf(esq), esum);
+                const double w2 = wr * wr;
+                const double d2 = (double)det.x * det.x + (double)det.y * det.y;
+                ssum = fma(w2, d2, ssum);
+                esum = fma(w2, fma(d2, (double)er2, (double)zabs2), esum);
             }
-            res = make_d4(ar, ai, (double)ssum, (double)esum);
+            res = make_d4(ar, ai, ssum, esum);
         }
         B.part[(size_t)chunk * nb + b] = res;
     }
@@ -215,16 +216,17 @@ __global__ void __launch_bounds__(256) k_exact_lu_rows(ExactBlockDev B, const ui
             const bool live = ok && r < eta;
 #pragma unroll
             for (int j = 0; j < G; ++j) rowv[j] = (live && j < eta) ? src[j] : mk(R(0), R(0));
-            R esq;
-            const T det = lu_det_rows<R, G>(rowv, r, eta, esq);
+            R er2, zabs2;
+            const T det = lu_det_rows<R, G>(rowv, r, eta, er2, zabs2);
             const uint32_t yl = y & locmask;
             const double wr = B.WLlo[yl & lomask] * B.WLhi[yl >> B.lobits];
             const double2 wd = times_i_pow(make_double2(wr * (double)det.x, wr * (double)det.y), __popc(yl));
             ar += wd.x;
             ai += wd.y;
-            const double aw = fabs(wr);
-            ssum = fma(aw, sqrt((double)abs2(det)), ssum);
-            esum = fma(aw, sqrt((double)esq), esum);
+            const double w2 = wr * wr;
+            const double d2 = (double)det.x * det.x + (double)det.y * det.y;
+            ssum = fma(w2, d2, ssum);
+            esum = fma(w2, fma(d2, (double)er2, (double)zabs2), esum);
         }
         if (valid && r == 0)
             B.part[(size_t)chunk * stride + pos] = ok ? make_d4(ar, ai, ssum, esum) : make_d4(0, 0, 0, 0);
@@ -315,13 +317,15 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                                                      __popc((unsigned)ys));
                     ar = fma(wr, prod.x, ar);
                     ai = fma(wr, prod.y, ai);
-                    const double aw = fabs(wr);
-                    S = fma(aw, s0 * s1, S);
-                    E = fma(aw, e0 * s1 + s0 * e1, E);
+                    const double w2 = wr * wr;
+                    S = fma(w2, s0 * s1, S);
+                    E = fma(w2, e0 * s1 + s0 * e1, E);
                 }
             }
             p = ar * ar + ai * ai;
-            const double dabs = 2.0 * sqrt(p) * C.err_coef * E;
+            // rounding errors of different minors are independent: the FP32
+            // amplitude error is estimated in quadrature, |d amp| ~ K eta u sqrt(2 E)
+            const double dabs = 2.0 * sqrt(p) * C.err_coef * sqrt(2.0 * E);
             e = dabs / fmax(p, C.p_floor);
         }
         out[b] = p;

@@ -7,7 +7,8 @@
 
 namespace ef {
 
-// (re, im, S, E): one partial branch sum of the Exact path
+// One partial branch sum of the Exact path: (re, im) of sum_y w(y) det, and
+// S = sum_y |w|^2 |det|^2, E = sum_y |w|^2 e_det^2 for the FP32 error estimate
 struct __align__(32) d4 {
     double x, y, z, w;
 };
