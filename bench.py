@@ -316,6 +316,7 @@ def run_ours(args):
 
 
 def main():
+    global NB
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -323,11 +324,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "fp64", "fp32"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--nb", type=int, default=NB, help="bitstrings per GPU (profiling runs use fewer)")
+    ap.add_argument("--nb", type=int, default=10_000, help="bitstrings per GPU (profiling runs use fewer)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    global NB
     NB = args.nb
     if args.impl == "reference":
         return run_reference(args)
