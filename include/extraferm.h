@@ -179,6 +179,30 @@ int ef_prob_grad(ef_circuit* c, const uint64_t* bits, int64_t nb, const double* 
 int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_grad_p,
                      double* d_out_p, double* d_grad_angles, void* stream);
 
+/* Exact algorithm like ef_prob_exact_dev, for callers that cannot let a
+ * library allocate GPU memory while they run: for example a service that
+ * hands all device memory to its own pool at start-up (a later cudaMalloc
+ * would fail or evict its data), or a latency-bound loop in which a
+ * cudaMalloc/cudaFree would synchronise the device and stall other streams.
+ * The paper has no counterpart; this is an interface of this library.
+ *
+ * Everything the call needs on the device (circuit tables, branch
+ * matrices, partial sums, the recompute list) is carved from one fixed
+ * 64 MiB array declared at file scope in the library, which every GPU that
+ * loads the library holds until the process exits. The call itself performs
+ * no cudaMalloc, cudaFree or other allocating call; the caller still passes
+ * the bitstrings and outputs (device pointers). The first call on a device
+ * looks the array's device address up (cudaGetSymbolAddress with that device
+ * current); make that first call before any stream capture. Calls whose
+ * tables, branch matrices and per-bitstring partials do not fit return
+ * EF_EINVAL with the largest batch that fits; split the batch. All calls
+ * (on any circuit and any stream) share the array and it keeps the last
+ * call's contents, so calls that overlap on the GPU race: order them on one
+ * stream or synchronise between them. The circuit's stats of the call are
+ * available from ef_circuit_get_stats (no kernel timing). */
+int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out,
+                              double* d_err_out, void* stream);
+
 /* Counters and timings of the circuit's last probability call (waits for it). */
 int ef_circuit_get_stats(ef_circuit* c, ef_stats* st);
 

@@ -69,6 +69,7 @@ SIGNATURES = {
     "ef_prob_grad": (ctypes.c_int, [_P, _U64P, _I64, _DP, _DP, _DP]),
     "ef_prob_grad_dev": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "ef_circuit_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(EfStats)]),
+    "ef_prob_exact_noalloc_dev": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
 }
 
 _lib = None
@@ -189,6 +190,13 @@ def ef_prob_exact(c, bits, want_err: bool = False):
 
 def ef_prob_exact_dev(c, d_bits: int, nb: int, d_out: int, d_err: int = 0, stream: int = 0):
     _check(load().ef_prob_exact_dev(c, d_bits, nb, d_out, d_err or None, stream or None))
+
+
+def ef_prob_exact_noalloc_dev(c, d_bits: int, nb: int, d_out: int, d_err: int = 0, stream: int = 0):
+    """Exact probabilities without any device allocation by the library: all
+    scratch comes from the library's fixed 64 MiB per-GPU array (see
+    extraferm.h for who needs this, the size limit and the ordering rule)."""
+    _check(load().ef_prob_exact_noalloc_dev(c, d_bits, nb, d_out, d_err or None, stream or None))
 
 
 def ef_prob_approx(c, bits, n_traj: int, seed: int = 0, index_base: int = 0, want_stderr: bool = True):

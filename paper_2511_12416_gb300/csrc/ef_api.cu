@@ -1001,3 +1001,223 @@ int ef_circuit_get_stats(ef_circuit* c, ef_stats* st) {
 }
 
 }  // extern "C"
+
+// =================================================================== allocation-free Exact entry point
+//
+// ef_prob_exact_noalloc_dev runs the same kernels as ef_prob_exact_dev but
+// takes every device buffer it needs (circuit tables, branch matrices,
+// partial sums, the recompute list) from one fixed array that the library
+// declares at file scope. It is for callers that must not have a library
+// allocate device memory during their run (see extraferm.h).
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB per GPU, held until the process exits
+constexpr int kNoAllocMaxDevices = 64;
+
+// File-scope scratch. In host code this name is only a stand-in for the
+// device symbol; kernels get its device address from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch on the current device (set up once per device).
+int noalloc_base(unsigned char** out) {
+    int dev = -1;
+    EF_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(EF_EUNSUPPORTED, "device index above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return fail(EF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return EF_OK;
+}
+
+__global__ void k_gather_columns(const double2* __restrict__ S0, const int* __restrict__ cols, int n, int eta,
+                                 double2* __restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * eta; e += gridDim.x * blockDim.x) {
+        const int i = e / eta, c = e - i * eta;
+        out[e] = S0[(size_t)i * n + cols[c]];
+    }
+}
+
+// Carves 256-byte aligned regions out of the scratch; only sizes on the first pass.
+struct Carver {
+    unsigned char* base;
+    size_t off = 0;
+    template <typename T> T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct NoAllocPlan {
+    double2* S0[ef::kMaxBlocks];
+    int* cols[ef::kMaxBlocks];
+    ef::ExactBlockDev blk[ef::kMaxBlocks];
+    double* WSlo;
+    double* WShi;
+    int* list;
+    int* count;
+};
+
+size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* base, NoAllocPlan& pl) {
+    Carver cv{base};
+    const int k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        const size_t nn = (size_t)B.n * B.n;
+        const int kB = B.k_loc + k_sh;
+        const size_t ny = (size_t)1 << kB;
+        const size_t ne = (size_t)B.n * B.eta;
+        ef::ExactBlockDev& d = pl.blk[b];
+        d = ef::ExactBlockDev{};
+        d.n = B.n;
+        d.eta = B.eta;
+        d.L = B.L;
+        d.k_loc = B.k_loc;
+        d.k_sh = k_sh;
+        d.c_log2 = B.c_log2;
+        d.lobits = B.lobits;
+        d.mask0 = B.mask[0];
+        d.mask1 = B.mask[1];
+        d.n_chunks = 1 << (kB - B.c_log2);
+        pl.S0[b] = cv.take<double2>(nn);
+        pl.cols[b] = cv.take<int>(B.cols.size());
+        d.S0C = cv.take<double2>(ne);
+        d.T = cv.take<double2>((size_t)B.L * nn);
+        d.F = cv.take<uint32_t>(B.F.size());
+        d.WLlo = cv.take<double>(B.WLlo.size());
+        d.WLhi = cv.take<double>(B.WLhi.size());
+        d.M64 = cv.take<double2>(ny * ne);
+        d.M32 = want32 ? cv.take<float2>(ny * ne) : nullptr;
+        d.part = cv.take<ef::d4>((size_t)d.n_chunks * (size_t)nb);
+    }
+    pl.WSlo = cv.take<double>(c->WSlo.size());
+    pl.WShi = cv.take<double>(c->WShi.size());
+    pl.list = cv.take<int>((size_t)nb);
+    pl.count = cv.take<int>(1);
+    return (cv.off + 255) & ~(size_t)255;
+}
+
+template <typename T>
+cudaError_t copy_in(T* dst, const std::vector<T>& src, cudaStream_t s) {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace
+
+extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out,
+                                         double* d_err_out, void* stream) {
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    if (nb < 0 || (nb > 0 && (!d_bits || !d_out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
+    if (!c->exact_ok) return fail(EF_EUNSUPPORTED, c->exact_why);
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int prec = c->opt.precision;
+    const bool fp64_only = prec == EF_PREC_FP64;
+    const bool autofix = prec == EF_PREC_AUTO;
+    NoAllocPlan pl{};
+    const size_t need = noalloc_layout(c, nb, !fp64_only, nullptr, pl);
+    if (need > kNoAllocBytes) {
+        const size_t fixed = noalloc_layout(c, 0, !fp64_only, nullptr, pl);
+        const size_t per = nb > 0 ? (need - fixed) / (size_t)nb + 1 : 1;
+        const int64_t fit = fixed < kNoAllocBytes ? (int64_t)((kNoAllocBytes - fixed) / per) : 0;
+        return fail(EF_EINVAL, "ef_prob_exact_noalloc_dev: this call needs " + std::to_string(need) +
+                                   " bytes of scratch, the fixed scratch holds " + std::to_string(kNoAllocBytes) +
+                                   "; pass at most " + std::to_string(fit) + " bitstrings per call for this circuit");
+    }
+    unsigned char* base = nullptr;
+    int rc = noalloc_base(&base);
+    if (rc) return rc;
+    noalloc_layout(c, nb, !fp64_only, base, pl);
+
+    if (c->has_last_stream && c->last_stream != s) EF_CK(cudaStreamSynchronize(c->last_stream));
+    c->last_stream = s;
+    c->has_last_stream = true;
+    c->stats = ef_stats{};
+    c->last_mode = 1;
+    c->last_fp64_list_pending = 0;
+    c->timed = false;
+    c->stats.logical_branch_dets = nb * (int64_t)std::ldexp(1.0, (int)c->cps.size());
+    if (nb == 0) return EF_OK;
+
+    ef::LaunchStats st;
+    int64_t sub_total = 0;
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        const size_t nn = (size_t)B.n * B.n;
+        EF_CK(cudaMemcpyAsync(pl.S0[b], B.S.data(), nn * sizeof(double2), cudaMemcpyHostToDevice, s));
+        EF_CK(copy_in(pl.cols[b], B.cols, s));
+        if (B.L > 0)
+            EF_CK(cudaMemcpyAsync(const_cast<double2*>(pl.blk[b].T), B.T.data() + nn, (size_t)B.L * nn * sizeof(double2),
+                                  cudaMemcpyHostToDevice, s));
+        EF_CK(copy_in(const_cast<uint32_t*>(pl.blk[b].F), B.F, s));
+        EF_CK(copy_in(const_cast<double*>(pl.blk[b].WLlo), B.WLlo, s));
+        EF_CK(copy_in(const_cast<double*>(pl.blk[b].WLhi), B.WLhi, s));
+        k_gather_columns<<<32, 128, 0, s>>>(pl.S0[b], pl.cols[b], B.n, B.eta, const_cast<double2*>(pl.blk[b].S0C));
+        EF_CK(cudaGetLastError());
+        st.launches += 1;
+        sub_total += (int64_t)1 << (B.k_loc + pl.blk[b].k_sh);
+    }
+    EF_CK(copy_in(pl.WSlo, c->WSlo, s));
+    EF_CK(copy_in(pl.WShi, c->WShi, s));
+    c->last_sub_total = sub_total;
+
+    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_build_branches(pl.blk[b], !fp64_only, s, st));
+
+    ef::ExactCombineDev cm{};
+    cm.nblocks = c->nblocks;
+    cm.k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
+    cm.shlobits = c->shlobits;
+    cm.WSlo = pl.WSlo;
+    cm.WShi = pl.WShi;
+    cm.inactive0 = c->inactive[0];
+    cm.inactive1 = c->inactive[1];
+    for (int b = 0; b < c->nblocks; ++b) {
+        cm.mask[b][0] = c->blk[b].mask[0];
+        cm.mask[b][1] = c->blk[b].mask[1];
+        cm.eta[b] = c->blk[b].eta;
+        cm.c_log2[b] = c->blk[b].c_log2;
+        cm.k_loc[b] = c->blk[b].k_loc;
+        cm.part[b] = pl.blk[b].part;
+        cm.eta_max = std::max(cm.eta_max, c->blk[b].eta);
+    }
+    cm.tol = c->opt.tol;
+    cm.p_floor = c->p_floor;
+    const double K = c->opt.tile_override[1] > 0 ? 0.1 * c->opt.tile_override[1] : 3.0;
+    cm.err_coef = fp64_only ? 0.0 : K * std::ldexp(1.0, -24);
+
+    for (int b = 0; b < c->nblocks; ++b) {
+        const ef::ExactBlockDev& d = pl.blk[b];
+        if (fp64_only) {
+            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, nullptr, nullptr, nb, true, s, st));
+        } else if (d.eta <= ef::kMaxEtaThread) {
+            EF_CK(ef::launch_exact_lu_f32(d, d_bits, nb, s, st));
+        } else {
+            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, nullptr, nullptr, nb, false, s, st));
+        }
+    }
+    // the scratch keeps the previous call's contents: the recompute list count starts at zero
+    EF_CK(cudaMemsetAsync(pl.count, 0, sizeof(int), s));
+    EF_CK(ef::launch_exact_combine(cm, d_bits, nb, nullptr, nullptr, d_out, d_err_out, autofix ? pl.list : nullptr,
+                                   autofix ? pl.count : nullptr, s, st));
+    if (autofix) {
+        for (int b = 0; b < c->nblocks; ++b)
+            EF_CK(ef::launch_exact_lu_rows(pl.blk[b], d_bits, nb, pl.list, pl.count, nb, true, s, st));
+        cm.err_coef = 0.0;
+        EF_CK(ef::launch_exact_combine(cm, d_bits, nb, pl.list, pl.count, d_out, d_err_out, nullptr, nullptr, s, st));
+    }
+    c->stats.kernel_launches = st.launches;
+    c->stats.executed_minor_lus = st.executed_lus;
+    return EF_OK;
+}
