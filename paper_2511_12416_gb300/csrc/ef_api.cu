@@ -8,7 +8,8 @@
 //   * per block, the passive segments S_0..S_L between the runs of
 //     controlled-phase gates that touch the block, and T_l = S_l diag(base
 //     phases e^{i theta/2} of layer l) (Section IV-B, Eqs. 14-18);
-//   * Exact: sub-branch bit layout, flip masks and weight tables;
+//   * Exact: GF(2) basis of the blocks' flip patterns, pattern flip masks,
+//     pattern weights of the local gates and the shared-gate tables;
 //   * Raw Estimate: interval products Pi_{a..b} = T_a ... T_b.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -97,37 +98,27 @@ struct HostBlock {
     std::vector<cd> T;       // (L+1) n x n: T_0 = S_0, T_l = S_l diag(D_l0)
     // Exact
     int k_loc = 0;
-    std::vector<int> local_gates;  // cphase indices, bits 0..k_loc-1
-    std::vector<uint32_t> F;       // L x n
-    std::vector<double> WLlo, WLhi;
-    int lobits = 0;
+    std::vector<int> local_gates;  // cphase indices local to the block
+    int r = 0, r_loc = 0;          // rank of the flip patterns / of the local gates' patterns
+    std::vector<uint32_t> F;       // L x n: flip masks over pattern bits
+    std::vector<cd> Omega;         // 2^r_loc: weights of the local gates folded onto patterns
+    std::vector<float2> Omega32;   // FP32 copy (error estimate)
+    std::vector<uint32_t> sh;      // 2^k_sh: pattern of each shared bit vector
+    std::vector<uint32_t> perm, goff;  // shared bit vectors grouped by pattern >> r_loc
     int c_log2 = 0;
     // Raw Estimate
     std::vector<cd> P;   // tri(L) x n x n
     std::vector<cd> RC;  // L x n x eta
     // device
-    DBuf dS0C, dT, dF, dWLlo, dWLhi, dM64, dM32, dPart, dP64, dP32, dRC64, dRC32, dCols;
+    DBuf dS0C, dT, dF, dOmega, dOmega32, dSh, dPerm, dGoff, dM64, dM32, dD, dP64, dP32, dRC64, dRC32, dCols;
     void release() {
-        for (DBuf* b : {&dS0C, &dT, &dF, &dWLlo, &dWLhi, &dM64, &dM32, &dPart, &dP64, &dP32, &dRC64, &dRC32, &dCols})
+        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dSh, &dPerm, &dGoff, &dM64, &dM32, &dD, &dP64, &dP32, &dRC64,
+                        &dRC32, &dCols})
             b->release();
     }
 };
 
 int tri(int a, int b) { return a * (a + 1) / 2 + b; }
-
-void split_table(const std::vector<double>& factors0, const std::vector<double>& factors1, int& lobits,
-                 std::vector<double>& lo, std::vector<double>& hi) {
-    // w(y) = prod_i (bit_i ? factors1[i] : factors0[i]) = lo[y & (2^lobits-1)] * hi[y >> lobits]
-    const int k = (int)factors0.size();
-    lobits = k / 2;
-    const int hib = k - lobits;
-    lo.assign((size_t)1 << lobits, 1.0);
-    hi.assign((size_t)1 << hib, 1.0);
-    for (size_t y = 0; y < lo.size(); ++y)
-        for (int i = 0; i < lobits; ++i) lo[y] *= ((y >> i) & 1) ? factors1[i] : factors0[i];
-    for (size_t y = 0; y < hi.size(); ++y)
-        for (int i = 0; i < hib; ++i) hi[y] *= ((y >> i) & 1) ? factors1[lobits + i] : factors0[lobits + i];
-}
 
 double log_binom(int n, int k) { return std::lgamma(n + 1.0) - std::lgamma(k + 1.0) - std::lgamma(n - k + 1.0); }
 
@@ -147,8 +138,8 @@ struct ef_circuit {
     HostBlock blk[ef::kMaxBlocks];
     uint64_t inactive[2] = {0, 0};
     std::vector<int> shared_gates;
-    std::vector<double> WSlo, WShi;
-    int shlobits = 0;
+    std::vector<cd> WS;  // 2^k_sh weights of the shared gates
+    std::vector<float2> WS32;
     bool exact_ok = true;
     std::string exact_why;
     bool approx_ok = true;
@@ -162,7 +153,7 @@ struct ef_circuit {
     double R0 = 1.0;
 
     bool dirty = true;
-    DBuf dWSlo, dWShi, dList, dListCount, dMaxErr, dBits, dOut, dErr, dGradP, dGrad;
+    DBuf dWS, dWS32, dList, dListCount, dRecomp, dBits, dOut, dErr, dGradP, dGrad;
     DBuf daT, daq, dalayer, damodes, daPart, dCounters;
     cudaStream_t own_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -170,13 +161,14 @@ struct ef_circuit {
     cudaStream_t last_stream = nullptr;
     bool has_last_stream = false;  // the legacy default stream is a null handle
     ef_stats stats{};
-    int64_t last_fp64_list_pending = 0;  // 1 if the fp64 list count must be read back
-    int64_t last_sub_total = 0;          // sum over blocks of 2^k_B (for executed-LU accounting)
+    int64_t last_fp64_list_pending = 0;  // 1 if the FP64 recompute count must be read back
+    int64_t last_sub_total = 0;          // sum over blocks of 2^r (minors per bitstring)
+    int* last_recomp = nullptr;          // device counter of the last call's FP64 recomputes
     int last_mode = 0;                   // 1 exact, 2 approx
 
     ~ef_circuit() {
         for (int b = 0; b < ef::kMaxBlocks; ++b) blk[b].release();
-        for (DBuf* d : {&dWSlo, &dWShi, &dList, &dListCount, &dMaxErr, &dBits, &dOut, &dErr, &dGradP, &dGrad, &daT,
+        for (DBuf* d : {&dWS, &dWS32, &dList, &dListCount, &dRecomp, &dBits, &dOut, &dErr, &dGradP, &dGrad, &daT,
                         &daq, &dalayer, &damodes, &daPart, &dCounters})
             d->release();
         if (ev0) cudaEventDestroy(ev0);
@@ -374,54 +366,126 @@ int prepare(ef_circuit* c) {
                 for (int m = 0; m < nb_; ++m) B.T[l * nn + (size_t)i * nb_ + m] = segs[l][(size_t)i * nb_ + m] * d[m];
         }
 
-        // ---- Exact: local gate bits, flip masks, weight tables
+        // ---- Exact: flip patterns. A gate's pattern is the set of (layer, local
+        // mode) pairs whose sign it flips; a trajectory's minor in this block
+        // depends only on the XOR of its flipped gates' patterns. Local gates
+        // come first so that the first r_loc basis patterns span theirs.
         B.local_gates.clear();
         for (int jj = 0; jj < k; ++jj)
             if (c->cps[jj].cls == b) B.local_gates.push_back(jj);
         B.k_loc = (int)B.local_gates.size();
-        const int kB = B.k_loc + (c->nblocks == 2 ? k_sh : 0);
-        if (kB > ef::kMaxExactSubBits) {
+        std::vector<int> gates_B = B.local_gates;
+        if (c->nblocks == 2) gates_B.insert(gates_B.end(), c->shared_gates.begin(), c->shared_gates.end());
+        const int PW = std::max(1, (L * nb_ + 63) / 64);
+        auto pattern = [&](int jj) {
+            std::vector<uint64_t> v(PW, 0);
+            const CP& cp = c->cps[jj];
+            const int l = layer_of_cp[jj] - 1;
+            if (l >= 0) {
+                if (cp.blk_p == b) {
+                    const int bit = l * nb_ + local_of[cp.p];
+                    v[bit >> 6] ^= 1ull << (bit & 63);
+                }
+                if (cp.blk_q == b) {
+                    const int bit = l * nb_ + local_of[cp.q];
+                    v[bit >> 6] ^= 1ull << (bit & 63);
+                }
+            }
+            return v;
+        };
+        struct EchelonRow {
+            std::vector<uint64_t> vec;
+            uint32_t comb;
+            int piv;
+        };
+        std::vector<EchelonRow> ech;
+        std::vector<std::vector<uint64_t>> basis;
+        std::vector<uint32_t> coord(gates_B.size(), 0);
+        bool too_many = false;
+        B.r_loc = 0;
+        for (size_t gi = 0; gi < gates_B.size(); ++gi) {
+            std::vector<uint64_t> v = pattern(gates_B[gi]);
+            uint32_t acc = 0;
+            for (const EchelonRow& e : ech)
+                if ((v[e.piv >> 6] >> (e.piv & 63)) & 1ull) {
+                    for (int w = 0; w < PW; ++w) v[w] ^= e.vec[w];
+                    acc ^= e.comb;
+                }
+            int piv = -1;
+            for (int w = 0; w < PW && piv < 0; ++w)
+                if (v[w]) piv = w * 64 + __builtin_ctzll(v[w]);
+            if (piv >= 0) {
+                const int t = (int)basis.size();
+                if (t >= ef::kMaxExactPatternBits) {
+                    too_many = true;
+                    break;
+                }
+                basis.push_back(pattern(gates_B[gi]));
+                ech.push_back({v, acc ^ (1u << t), piv});
+                coord[gi] = 1u << t;
+            } else {
+                coord[gi] = acc;
+            }
+            if ((int)gi + 1 == B.k_loc) B.r_loc = (int)basis.size();
+        }
+        B.r = (int)basis.size();
+        if (too_many || B.k_loc > ef::kMaxExactLocalBits || (c->nblocks == 2 && k_sh > ef::kMaxExactSharedBits)) {
             c->exact_ok = false;
-            c->exact_why = "Exact mode: a mode block has " + std::to_string(kB) +
-                           " controlled-phase gates; this build enumerates at most 2^" +
-                           std::to_string(ef::kMaxExactSubBits) + " sub-branches per block";
+            c->exact_why = "Exact mode: a mode block needs more than 2^" + std::to_string(ef::kMaxExactPatternBits) +
+                           " flip patterns, more than " + std::to_string(ef::kMaxExactLocalBits) +
+                           " local or more than " + std::to_string(ef::kMaxExactSharedBits) +
+                           " shared controlled-phase gates";
         }
         if (B.eta > ef::kMaxEtaRows) {
             c->exact_ok = false;
             c->exact_why = "Exact mode: more than 32 particles in one mode block";
         }
-        std::vector<int> ybit(k, -1);
-        for (int i = 0; i < B.k_loc; ++i) ybit[B.local_gates[i]] = i;
-        if (c->nblocks == 2)
-            for (int i = 0; i < k_sh; ++i) ybit[c->shared_gates[i]] = B.k_loc + i;
         B.F.assign((size_t)L * nb_, 0u);
-        for (int l = 1; l <= L; ++l)
-            for (int jj : B.layers[l - 1]) {
-                const CP& cp = c->cps[jj];
-                if (ybit[jj] < 0 || ybit[jj] >= 32) continue;
-                const uint32_t bit = 1u << ybit[jj];
-                if (cp.blk_p == b) B.F[(size_t)(l - 1) * nb_ + local_of[cp.p]] ^= bit;
-                if (cp.blk_q == b) B.F[(size_t)(l - 1) * nb_ + local_of[cp.q]] ^= bit;
+        for (int t = 0; t < B.r; ++t)
+            for (int bit = 0; bit < L * nb_; ++bit)
+                if ((basis[t][bit >> 6] >> (bit & 63)) & 1ull) B.F[bit] |= 1u << t;
+        B.Omega.clear();
+        B.Omega32.clear();
+        B.sh.clear();
+        B.perm.clear();
+        B.goff.clear();
+        if (c->exact_ok) {
+            // Omega(z) = sum of w_loc(y) over the local bit vectors y with pattern z
+            static const cd ipow[4] = {cd(1, 0), cd(0, 1), cd(-1, 0), cd(0, -1)};
+            B.Omega.assign((size_t)1 << B.r_loc, cd(0, 0));
+            const uint64_t nyl = 1ull << B.k_loc;
+            for (uint64_t y = 0; y < nyl; ++y) {
+                uint32_t z = 0;
+                double w = 1.0;
+                for (int i = 0; i < B.k_loc; ++i) {
+                    const CP& cp = c->cps[B.local_gates[i]];
+                    if ((y >> i) & 1ull) {
+                        z ^= coord[i];
+                        w *= cp.s;
+                    } else {
+                        w *= cp.c;
+                    }
+                }
+                B.Omega[z] += w * ipow[__builtin_popcountll(y) & 3];
             }
-        if (kB <= ef::kMaxExactSubBits) {
-            std::vector<double> f0, f1;
-            for (int jj : B.local_gates) {
-                f0.push_back(c->cps[jj].c);
-                f1.push_back(c->cps[jj].s);
+            B.Omega32.resize(B.Omega.size());
+            for (size_t z = 0; z < B.Omega.size(); ++z)
+                B.Omega32[z] = make_float2((float)B.Omega[z].real(), (float)B.Omega[z].imag());
+            const int ksh_b = c->nblocks == 2 ? k_sh : 0;
+            B.sh.assign((size_t)1 << ksh_b, 0u);
+            for (uint32_t xs = 0; xs < (1u << ksh_b); ++xs) {
+                uint32_t z = 0;
+                for (int i = 0; i < ksh_b; ++i)
+                    if ((xs >> i) & 1u) z ^= coord[B.k_loc + i];
+                B.sh[xs] = z;
             }
-            split_table(f0, f1, B.lobits, B.WLlo, B.WLhi);
-        } else {
-            B.WLlo.assign(1, 1.0);
-            B.WLhi.assign(1, 1.0);
-            B.lobits = 0;
-        }
-        // chunk of sub-branches handled per FP32 CTA: fit the chunk in 48 KB of shared memory
-        {
-            int cl = std::min(B.k_loc, 5);
-            if (c->opt.tile_override[0] > 0) cl = std::min(B.k_loc, c->opt.tile_override[0]);
-            if (B.eta <= ef::kMaxEtaThread)
-                while (cl > 0 && ((size_t)1 << cl) * nb_ * (size_t)(B.eta | 1) * 8 > 48 * 1024) --cl;
-            B.c_log2 = cl;
+            const uint32_t ngroups = 1u << (B.r - B.r_loc);
+            B.goff.assign(ngroups + 1, 0u);
+            for (uint32_t xs = 0; xs < B.sh.size(); ++xs) B.goff[(B.sh[xs] >> B.r_loc) + 1]++;
+            for (uint32_t g = 0; g < ngroups; ++g) B.goff[g + 1] += B.goff[g];
+            B.perm.assign(B.sh.size(), 0u);
+            std::vector<uint32_t> fill(B.goff.begin(), B.goff.end() - 1);
+            for (uint32_t xs = 0; xs < B.sh.size(); ++xs) B.perm[fill[B.sh[xs] >> B.r_loc]++] = xs;
         }
 
         // ---- Raw Estimate: interval products and right factors
@@ -466,19 +530,23 @@ int prepare(ef_circuit* c) {
             c->amodes[(size_t)b * k + jj] = (nb_ <= 64) ? mm : 0;
         }
     }
-    // shared weight table
-    if (k_sh <= ef::kMaxExactSubBits) {
-        std::vector<double> f0, f1;
-        if (c->nblocks == 2)
-            for (int jj : c->shared_gates) {
-                f0.push_back(c->cps[jj].c);
-                f1.push_back(c->cps[jj].s);
+    // shared weight table: w_sh(x_sh) = i^|x_sh| prod_j (x_j ? s_j : c_j)
+    c->WS.clear();
+    if (c->exact_ok) {
+        const int ksh_b = c->nblocks == 2 ? k_sh : 0;
+        c->WS.assign((size_t)1 << ksh_b, cd(0, 0));
+        static const cd ipow[4] = {cd(1, 0), cd(0, 1), cd(-1, 0), cd(0, -1)};
+        for (uint32_t xs = 0; xs < (1u << ksh_b); ++xs) {
+            double w = 1.0;
+            for (int i = 0; i < ksh_b; ++i) {
+                const CP& cp = c->cps[c->shared_gates[i]];
+                w *= ((xs >> i) & 1u) ? cp.s : cp.c;
             }
-        split_table(f0, f1, c->shlobits, c->WSlo, c->WShi);
-    } else {
-        c->WSlo.assign(1, 1.0);
-        c->WShi.assign(1, 1.0);
-        c->shlobits = 0;
+            c->WS[xs] = w * ipow[__builtin_popcount(xs) & 3];
+        }
+        c->WS32.resize(c->WS.size());
+        for (size_t x = 0; x < c->WS.size(); ++x)
+            c->WS32[x] = make_float2((float)c->WS[x].real(), (float)c->WS[x].imag());
     }
     c->p_floor = 1e-6 * std::exp(-log_sector);
     // approx gate tables
@@ -495,41 +563,43 @@ int prepare(ef_circuit* c) {
     return EF_OK;
 }
 
+std::vector<double2> to_d2(const std::vector<cd>& v, size_t off = 0, size_t count = (size_t)-1) {
+    const size_t n = std::min(count, v.size() - std::min(off, v.size()));
+    std::vector<double2> o(n);
+    for (size_t i = 0; i < n; ++i) o[i] = make_double2(v[off + i].real(), v[off + i].imag());
+    return o;
+}
+
 int upload_tables(ef_circuit* c, cudaStream_t s) {
     if (!c->dirty) return EF_OK;
     for (int b = 0; b < c->nblocks; ++b) {
         HostBlock& B = c->blk[b];
         const size_t nn = (size_t)B.n * B.n;
-        std::vector<double2> S0C((size_t)B.n * B.eta), T((size_t)B.L * nn);
+        std::vector<double2> S0C((size_t)B.n * B.eta);
         for (int i = 0; i < B.n; ++i)
             for (int cc = 0; cc < B.eta; ++cc) {
                 const cd v = B.S[(size_t)i * B.n + B.cols[cc]];
                 S0C[(size_t)i * B.eta + cc] = make_double2(v.real(), v.imag());
             }
-        for (size_t e = 0; e < (size_t)B.L * nn; ++e) T[e] = make_double2(B.T[nn + e].real(), B.T[nn + e].imag());
         EF_CK(upload(B.dS0C, S0C, s));
-        EF_CK(upload(B.dT, T, s));
+        EF_CK(upload(B.dT, to_d2(B.T, nn, (size_t)B.L * nn), s));
         EF_CK(upload(B.dF, B.F, s));
-        EF_CK(upload(B.dWLlo, B.WLlo, s));
-        EF_CK(upload(B.dWLhi, B.WLhi, s));
-        std::vector<double2> P64(B.P.size()), RC64(B.RC.size());
+        EF_CK(upload(B.dOmega, to_d2(B.Omega), s));
+        EF_CK(upload(B.dOmega32, B.Omega32, s));
+        EF_CK(upload(B.dSh, B.sh, s));
+        EF_CK(upload(B.dPerm, B.perm, s));
+        EF_CK(upload(B.dGoff, B.goff, s));
         std::vector<float2> P32(B.P.size()), RC32(B.RC.size());
-        for (size_t e = 0; e < B.P.size(); ++e) {
-            P64[e] = make_double2(B.P[e].real(), B.P[e].imag());
-            P32[e] = make_float2((float)B.P[e].real(), (float)B.P[e].imag());
-        }
-        for (size_t e = 0; e < B.RC.size(); ++e) {
-            RC64[e] = make_double2(B.RC[e].real(), B.RC[e].imag());
-            RC32[e] = make_float2((float)B.RC[e].real(), (float)B.RC[e].imag());
-        }
-        EF_CK(upload(B.dP64, P64, s));
+        for (size_t e = 0; e < B.P.size(); ++e) P32[e] = make_float2((float)B.P[e].real(), (float)B.P[e].imag());
+        for (size_t e = 0; e < B.RC.size(); ++e) RC32[e] = make_float2((float)B.RC[e].real(), (float)B.RC[e].imag());
+        EF_CK(upload(B.dP64, to_d2(B.P), s));
         EF_CK(upload(B.dP32, P32, s));
-        EF_CK(upload(B.dRC64, RC64, s));
+        EF_CK(upload(B.dRC64, to_d2(B.RC), s));
         EF_CK(upload(B.dRC32, RC32, s));
         EF_CK(upload(B.dCols, B.cols, s));
     }
-    EF_CK(upload(c->dWSlo, c->WSlo, s));
-    EF_CK(upload(c->dWShi, c->WShi, s));
+    EF_CK(upload(c->dWS, to_d2(c->WS), s));
+    EF_CK(upload(c->dWS32, c->WS32, s));
     std::vector<uint32_t> T4(((c->aT.size() + 3) & ~(size_t)3), 0u);
     std::copy(c->aT.begin(), c->aT.end(), T4.begin());
     EF_CK(upload(c->daT, T4, s));
@@ -582,6 +652,7 @@ int begin_call(ef_circuit* c, cudaStream_t s, int mode) {
     c->stats = ef_stats{};
     c->last_mode = mode;
     c->last_fp64_list_pending = 0;
+    c->last_recomp = nullptr;
     c->timed = (c->opt.flags & EF_FLAG_TIME_KERNELS) != 0;
     if (c->timed && !c->ev0) {
         EF_CK(cudaEventCreate(&c->ev0));
@@ -590,126 +661,175 @@ int begin_call(ef_circuit* c, cudaStream_t s, int mode) {
     return upload_tables(c, s);
 }
 
-ef::ExactBlockDev exact_block_dev(ef_circuit* c, int b) {
-    HostBlock& B = c->blk[b];
-    ef::ExactBlockDev d{};
+// Device buffers of one Exact call (from the circuit's workspace or from the
+// allocation-free scratch).
+struct ExactBuffers {
+    ef::ExactBlockDev blk[ef::kMaxBlocks];
+    const double2* Omega[ef::kMaxBlocks];
+    const float2* Omega32[ef::kMaxBlocks];
+    const uint32_t* sh[ef::kMaxBlocks];
+    const uint32_t* perm[ef::kMaxBlocks];
+    const uint32_t* goff[ef::kMaxBlocks];
+    const double2* WS;
+    const float2* WS32;
+    int* list;
+    int* count;
+    int* recomp;
+    int64_t cap;  // bitstrings per batch (row stride of the determinant buffers)
+};
+
+// Bitstrings per batch so that the per-(pattern, bitstring) determinants stay
+// within `budget` bytes.
+int64_t exact_batch(const ef_circuit* c, int64_t nb, size_t budget) {
+    size_t per = 0;
+    for (int b = 0; b < c->nblocks; ++b) per += ((size_t)1 << c->blk[b].r) * sizeof(ef::d4);
+    if (per == 0 || nb == 0) return std::max<int64_t>(nb, 1);
+    return std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)(budget / per)));
+}
+
+void exact_block_geometry(const ef_circuit* c, int b, int64_t cap, ef::ExactBlockDev& d) {
+    const HostBlock& B = c->blk[b];
     d.n = B.n;
     d.eta = B.eta;
     d.L = B.L;
-    d.k_loc = B.k_loc;
-    d.k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
-    d.c_log2 = B.c_log2;
-    d.lobits = B.lobits;
+    d.r = B.r;
+    d.r_loc = B.r_loc;
+    d.c_log2 = ef::exact_f32_chunk_log2(B.n, B.eta, B.r, cap);
+    d.n_chunks = 1 << (B.r - d.c_log2);
     d.mask0 = B.mask[0];
     d.mask1 = B.mask[1];
-    d.S0C = B.dS0C.as<double2>();
-    d.T = B.dT.as<double2>();
-    d.F = B.dF.as<uint32_t>();
-    d.WLlo = B.dWLlo.as<double>();
-    d.WLhi = B.dWLhi.as<double>();
-    d.M64 = B.dM64.as<double2>();
-    d.M32 = B.dM32.as<float2>();
-    d.part = B.dPart.as<ef::d4>();
-    d.n_chunks = 1 << (d.k_loc + d.k_sh - d.c_log2);
-    return d;
+}
+
+int run_exact(ef_circuit* c, const ExactBuffers& eb, const uint64_t* d_bits, int64_t nb, double* d_out,
+              double* d_err, cudaStream_t s, ef::LaunchStats& st) {
+    const int prec = c->opt.precision;
+    const bool fp64_only = prec == EF_PREC_FP64;
+    const bool autofix = prec == EF_PREC_AUTO;
+    double flops = 0.0;
+    int64_t sub_total = 0;
+    for (int b = 0; b < c->nblocks; ++b) {
+        flops += (double)nb * std::ldexp(1.0, c->blk[b].r) * lu_flops(c->blk[b].eta);
+        sub_total += (int64_t)1 << c->blk[b].r;
+    }
+    c->last_sub_total = sub_total;
+    c->stats.dominant_kernel_flops = flops;
+    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_build_branches(eb.blk[b], !fp64_only, s, st));
+
+    ef::ExactCombineDev cm{};
+    cm.nblocks = c->nblocks;
+    cm.k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
+    cm.inactive0 = c->inactive[0];
+    cm.inactive1 = c->inactive[1];
+    for (int b = 0; b < c->nblocks; ++b) {
+        cm.mask[b][0] = c->blk[b].mask[0];
+        cm.mask[b][1] = c->blk[b].mask[1];
+        cm.eta[b] = c->blk[b].eta;
+        cm.r[b] = c->blk[b].r;
+        cm.r_loc[b] = c->blk[b].r_loc;
+        cm.D[b] = eb.blk[b].D;
+        cm.Omega[b] = eb.Omega[b];
+        cm.Omega32[b] = eb.Omega32[b];
+        cm.s[b] = eb.sh[b];
+        cm.perm[b] = eb.perm[b];
+        cm.goff[b] = eb.goff[b];
+    }
+    cm.WS = eb.WS;
+    cm.WS32 = eb.WS32;
+    cm.tol = c->opt.tol;
+    cm.p_floor = c->p_floor;
+    // FP32 error model: per minor |d det|^2 ~ (K u32)^2 (|det|^2 er2 + zabs2),
+    // independent between distinct minors and propagated to the amplitude
+    // through each minor's coefficient. Observed errors behave like Gaussians
+    // whose standard deviation is about a third of the K = 1 estimate, so
+    // K = 4 bounds them at about 5 standard deviations (the largest ratio seen
+    // in 16,000 significant results was 0.76 at K = 4);
+    // ef_options.tile_override[1] > 0 sets K in tenths.
+    const double K = c->opt.tile_override[1] > 0 ? 0.1 * c->opt.tile_override[1] : 4.0;
+    const double err_coef = fp64_only ? 0.0 : K * std::ldexp(1.0, -24);
+    if (autofix) {
+        EF_CK(cudaMemsetAsync(eb.recomp, 0, sizeof(int), s));
+        c->last_recomp = eb.recomp;
+        c->last_fp64_list_pending = 1;
+    }
+    int64_t lu_launches = 0;
+    for (int64_t off = 0; off < nb; off += eb.cap) {
+        const int64_t nbb = std::min(eb.cap, nb - off);
+        const uint64_t* bits = d_bits + 2 * off;
+        double* out = d_out + off;
+        double* err = d_err ? d_err + off : nullptr;
+        if (c->timed && off == 0) EF_CK(cudaEventRecord(c->ev0, s));
+        const int64_t before = st.launches;
+        for (int b = 0; b < c->nblocks; ++b) {
+            const ef::ExactBlockDev& d = eb.blk[b];
+            if (fp64_only) {
+                EF_CK(ef::launch_exact_lu_f64(d, bits, nbb, nullptr, nullptr, nbb, s, st));
+            } else if (d.eta <= ef::kMaxEtaThread) {
+                EF_CK(ef::launch_exact_lu_f32(d, bits, nbb, s, st));
+            } else {
+                EF_CK(ef::launch_exact_lu_rows(d, bits, nbb, nullptr, nullptr, nbb, false, s, st));
+            }
+        }
+        lu_launches += st.launches - before;
+        if (c->timed && off + nbb >= nb) EF_CK(cudaEventRecord(c->ev1, s));
+        if (autofix) EF_CK(cudaMemsetAsync(eb.count, 0, sizeof(int), s));
+        cm.err_coef = err_coef;
+        cm.recomputed_total = nullptr;
+        EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, nullptr, nullptr, out, err, autofix ? eb.list : nullptr,
+                                       autofix ? eb.count : nullptr, s, st));
+        if (autofix) {
+            for (int b = 0; b < c->nblocks; ++b)
+                EF_CK(ef::launch_exact_lu_f64(eb.blk[b], bits, nbb, eb.list, eb.count, nbb, s, st));
+            cm.err_coef = 0.0;
+            cm.recomputed_total = eb.recomp;
+            EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, eb.list, eb.count, out, err, nullptr, nullptr, s, st));
+        }
+    }
+    c->stats.dominant_kernel_launches = lu_launches;
+    c->stats.kernel_launches = st.launches;
+    c->stats.executed_minor_lus = st.executed_lus;
+    return EF_OK;
 }
 
 int exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out, double* d_err, cudaStream_t s) {
     if (!c->exact_ok) return fail(EF_EUNSUPPORTED, c->exact_why);
     int rc = begin_call(c, s, 1);
     if (rc) return rc;
-    const int prec = c->opt.precision;
-    const bool fp64_only = prec == EF_PREC_FP64;
-    ef::LaunchStats st;
+    const bool fp64_only = c->opt.precision == EF_PREC_FP64;
     c->stats.logical_branch_dets = nb * (int64_t)std::ldexp(1.0, (int)c->cps.size());
     if (nb == 0) return EF_OK;
-    // workspaces
-    double flops = 0.0;
-    int64_t sub_total = 0;
+    ExactBuffers eb{};
+    eb.cap = exact_batch(c, nb, (size_t)2 << 30);
     for (int b = 0; b < c->nblocks; ++b) {
         HostBlock& B = c->blk[b];
-        const int kB = B.k_loc + (c->nblocks == 2 ? (int)c->shared_gates.size() : 0);
-        const size_t ny = (size_t)1 << kB;
+        const size_t ny = (size_t)1 << B.r;
         const size_t ne = (size_t)B.n * B.eta;
         EF_CK(B.dM64.ensure(ny * ne * sizeof(double2)));
         if (!fp64_only) EF_CK(B.dM32.ensure(ny * ne * sizeof(float2)));
-        const size_t nch = (size_t)1 << (kB - B.c_log2);
-        EF_CK(B.dPart.ensure(nch * (size_t)nb * sizeof(ef::d4)));
-        flops += (double)nb * (double)ny * lu_flops(B.eta);
-        sub_total += (int64_t)ny;
+        EF_CK(B.dD.ensure(ny * (size_t)eb.cap * sizeof(ef::d4)));
+        ef::ExactBlockDev& d = eb.blk[b];
+        exact_block_geometry(c, b, eb.cap, d);
+        d.S0C = B.dS0C.as<double2>();
+        d.T = B.dT.as<double2>();
+        d.F = B.dF.as<uint32_t>();
+        d.M64 = B.dM64.as<double2>();
+        d.M32 = fp64_only ? nullptr : B.dM32.as<float2>();
+        d.D = B.dD.as<ef::d4>();
+        eb.Omega[b] = B.dOmega.as<double2>();
+        eb.Omega32[b] = B.dOmega32.as<float2>();
+        eb.sh[b] = B.dSh.as<uint32_t>();
+        eb.perm[b] = B.dPerm.as<uint32_t>();
+        eb.goff[b] = B.dGoff.as<uint32_t>();
     }
-    c->last_sub_total = sub_total;
-    // builder
-    for (int b = 0; b < c->nblocks; ++b) {
-        ef::ExactBlockDev d = exact_block_dev(c, b);
-        EF_CK(ef::launch_build_branches(d, !fp64_only, s, st));
-    }
-    ef::ExactCombineDev cm{};
-    cm.nblocks = c->nblocks;
-    cm.k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
-    cm.shlobits = c->shlobits;
-    cm.WSlo = c->dWSlo.as<double>();
-    cm.WShi = c->dWShi.as<double>();
-    cm.inactive0 = c->inactive[0];
-    cm.inactive1 = c->inactive[1];
-    cm.eta_max = 0;
-    for (int b = 0; b < c->nblocks; ++b) {
-        cm.mask[b][0] = c->blk[b].mask[0];
-        cm.mask[b][1] = c->blk[b].mask[1];
-        cm.eta[b] = c->blk[b].eta;
-        cm.c_log2[b] = c->blk[b].c_log2;
-        cm.k_loc[b] = c->blk[b].k_loc;
-        cm.part[b] = c->blk[b].dPart.as<ef::d4>();
-        cm.eta_max = std::max(cm.eta_max, c->blk[b].eta);
-    }
-    cm.tol = c->opt.tol;
-    cm.p_floor = c->p_floor;
-    // FP32 error model: |d det|^2 ~ (K u32)^2 (|det|^2 er2 + zabs2) per minor,
-    // independent between minors (combined in quadrature). K = 3 covers the
-    // largest observed actual/estimated ratio (2.3 at K = 1) with margin;
-    // ef_options.tile_override[1] > 0 sets K in tenths.
-    const double K = c->opt.tile_override[1] > 0 ? 0.1 * c->opt.tile_override[1] : 3.0;
-    cm.err_coef = fp64_only ? 0.0 : K * std::ldexp(1.0, -24);
-
-    if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
-    const int64_t lu_launches_before = st.launches;
-    for (int b = 0; b < c->nblocks; ++b) {
-        ef::ExactBlockDev d = exact_block_dev(c, b);
-        if (fp64_only) {
-            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, nullptr, nullptr, nb, true, s, st));
-        } else if (d.eta <= ef::kMaxEtaThread) {
-            EF_CK(ef::launch_exact_lu_f32(d, d_bits, nb, s, st));
-        } else {
-            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, nullptr, nullptr, nb, false, s, st));
-        }
-    }
-    if (c->timed) EF_CK(cudaEventRecord(c->ev1, s));
-    c->stats.dominant_kernel_launches = st.launches - lu_launches_before;
-    c->stats.dominant_kernel_flops = flops;
-
-    const bool autofix = prec == EF_PREC_AUTO;
-    if (autofix) {
-        EF_CK(c->dList.ensure((size_t)nb * sizeof(int)));
-        EF_CK(c->dListCount.ensure(sizeof(int)));
-        EF_CK(cudaMemsetAsync(c->dListCount.p, 0, sizeof(int), s));
-    }
-    EF_CK(ef::launch_exact_combine(cm, d_bits, nb, nullptr, nullptr, d_out, d_err,
-                                   autofix ? c->dList.as<int>() : nullptr,
-                                   autofix ? c->dListCount.as<int>() : nullptr, s, st));
-    if (autofix) {
-        for (int b = 0; b < c->nblocks; ++b) {
-            ef::ExactBlockDev d = exact_block_dev(c, b);
-            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, c->dList.as<int>(), c->dListCount.as<int>(), nb, true, s,
-                                           st));
-        }
-        cm.err_coef = 0.0;
-        EF_CK(ef::launch_exact_combine(cm, d_bits, nb, c->dList.as<int>(), c->dListCount.as<int>(), d_out, d_err,
-                                       nullptr, nullptr, s, st));
-        c->last_fp64_list_pending = 1;
-    }
-    c->stats.kernel_launches = st.launches;
-    c->stats.executed_minor_lus = st.executed_lus;
-    return EF_OK;
+    eb.WS = c->dWS.as<double2>();
+    eb.WS32 = c->dWS32.as<float2>();
+    EF_CK(c->dList.ensure((size_t)eb.cap * sizeof(int)));
+    EF_CK(c->dListCount.ensure(sizeof(int)));
+    EF_CK(c->dRecomp.ensure(sizeof(int)));
+    eb.list = c->dList.as<int>();
+    eb.count = c->dListCount.as<int>();
+    eb.recomp = c->dRecomp.as<int>();
+    ef::LaunchStats st;
+    return run_exact(c, eb, d_bits, nb, d_out, d_err, s, st);
 }
 
 int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uint64_t seed, uint64_t base,
@@ -983,9 +1103,9 @@ int ef_circuit_get_stats(ef_circuit* c, ef_stats* st) {
         EF_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
         c->stats.dominant_kernel_ms = ms;
     }
-    if (c->last_mode == 1 && c->last_fp64_list_pending) {
+    if (c->last_mode == 1 && c->last_fp64_list_pending && c->last_recomp) {
         int cnt = 0;
-        EF_CK(cudaMemcpy(&cnt, c->dListCount.p, sizeof(int), cudaMemcpyDeviceToHost));
+        EF_CK(cudaMemcpy(&cnt, c->last_recomp, sizeof(int), cudaMemcpyDeviceToHost));
         c->stats.fp64_recomputed = cnt;
         c->stats.executed_minor_lus += (int64_t)cnt * c->last_sub_total;
         c->last_fp64_list_pending = 0;
@@ -1060,59 +1180,55 @@ struct Carver {
     }
 };
 
-struct NoAllocPlan {
+struct NoAllocTables {
     double2* S0[ef::kMaxBlocks];
     int* cols[ef::kMaxBlocks];
-    ef::ExactBlockDev blk[ef::kMaxBlocks];
-    double* WSlo;
-    double* WShi;
-    int* list;
-    int* count;
 };
 
-size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* base, NoAllocPlan& pl) {
+size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* base, ExactBuffers& eb,
+                      NoAllocTables& tb) {
     Carver cv{base};
-    const int k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
+    eb.cap = std::max<int64_t>(nb, 1);
     for (int b = 0; b < c->nblocks; ++b) {
         HostBlock& B = c->blk[b];
         const size_t nn = (size_t)B.n * B.n;
-        const int kB = B.k_loc + k_sh;
-        const size_t ny = (size_t)1 << kB;
+        const size_t ny = (size_t)1 << B.r;
         const size_t ne = (size_t)B.n * B.eta;
-        ef::ExactBlockDev& d = pl.blk[b];
+        ef::ExactBlockDev& d = eb.blk[b];
         d = ef::ExactBlockDev{};
-        d.n = B.n;
-        d.eta = B.eta;
-        d.L = B.L;
-        d.k_loc = B.k_loc;
-        d.k_sh = k_sh;
-        d.c_log2 = B.c_log2;
-        d.lobits = B.lobits;
-        d.mask0 = B.mask[0];
-        d.mask1 = B.mask[1];
-        d.n_chunks = 1 << (kB - B.c_log2);
-        pl.S0[b] = cv.take<double2>(nn);
-        pl.cols[b] = cv.take<int>(B.cols.size());
+        exact_block_geometry(c, b, eb.cap, d);
+        tb.S0[b] = cv.take<double2>(nn);
+        tb.cols[b] = cv.take<int>(B.cols.size());
         d.S0C = cv.take<double2>(ne);
         d.T = cv.take<double2>((size_t)B.L * nn);
         d.F = cv.take<uint32_t>(B.F.size());
-        d.WLlo = cv.take<double>(B.WLlo.size());
-        d.WLhi = cv.take<double>(B.WLhi.size());
+        eb.Omega[b] = cv.take<double2>(B.Omega.size());
+        eb.Omega32[b] = cv.take<float2>(B.Omega32.size());
+        eb.sh[b] = cv.take<uint32_t>(B.sh.size());
+        eb.perm[b] = cv.take<uint32_t>(B.perm.size());
+        eb.goff[b] = cv.take<uint32_t>(B.goff.size());
         d.M64 = cv.take<double2>(ny * ne);
         d.M32 = want32 ? cv.take<float2>(ny * ne) : nullptr;
-        d.part = cv.take<ef::d4>((size_t)d.n_chunks * (size_t)nb);
+        d.D = cv.take<ef::d4>(ny * (size_t)eb.cap);
     }
-    pl.WSlo = cv.take<double>(c->WSlo.size());
-    pl.WShi = cv.take<double>(c->WShi.size());
-    pl.list = cv.take<int>((size_t)nb);
-    pl.count = cv.take<int>(1);
+    eb.WS = cv.take<double2>(c->WS.size());
+    eb.WS32 = cv.take<float2>(c->WS32.size());
+    eb.list = cv.take<int>((size_t)eb.cap);
+    eb.count = cv.take<int>(1);
+    eb.recomp = cv.take<int>(1);
     return (cv.off + 255) & ~(size_t)255;
 }
 
 template <typename T>
-cudaError_t copy_in(T* dst, const std::vector<T>& src, cudaStream_t s) {
+cudaError_t copy_in(const T* dst, const std::vector<T>& src, cudaStream_t s) {
     if (src.empty()) return cudaSuccess;
-    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    return cudaMemcpyAsync(const_cast<T*>(dst), src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+// std::complex<double> has the layout of double2 (real, imaginary)
+cudaError_t copy_in_c(const double2* dst, const cd* src, size_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    return cudaMemcpyAsync(const_cast<double2*>(dst), src, count * sizeof(double2), cudaMemcpyHostToDevice, s);
 }
 
 }  // namespace
@@ -1121,17 +1237,17 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
                                          double* d_err_out, void* stream) {
     if (!c) return fail(EF_EINVAL, "NULL circuit");
     if (nb < 0 || (nb > 0 && (!d_bits || !d_out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
+    if (nb > 2147483647ll) return fail(EF_EINVAL, "more than 2^31-1 bitstrings per call");
     if (!c->exact_ok) return fail(EF_EUNSUPPORTED, c->exact_why);
     const cudaStream_t s = (cudaStream_t)stream;
-    const int prec = c->opt.precision;
-    const bool fp64_only = prec == EF_PREC_FP64;
-    const bool autofix = prec == EF_PREC_AUTO;
-    NoAllocPlan pl{};
-    const size_t need = noalloc_layout(c, nb, !fp64_only, nullptr, pl);
+    const bool fp64_only = c->opt.precision == EF_PREC_FP64;
+    ExactBuffers eb{};
+    NoAllocTables tb{};
+    const size_t need = noalloc_layout(c, nb, !fp64_only, nullptr, eb, tb);
     if (need > kNoAllocBytes) {
-        const size_t fixed = noalloc_layout(c, 0, !fp64_only, nullptr, pl);
-        const size_t per = nb > 0 ? (need - fixed) / (size_t)nb + 1 : 1;
-        const int64_t fit = fixed < kNoAllocBytes ? (int64_t)((kNoAllocBytes - fixed) / per) : 0;
+        const size_t fixed = noalloc_layout(c, 1, !fp64_only, nullptr, eb, tb);
+        const size_t per = nb > 1 ? (need - fixed) / (size_t)(nb - 1) + 1 : 1;
+        const int64_t fit = fixed < kNoAllocBytes ? 1 + (int64_t)((kNoAllocBytes - fixed) / per) : 0;
         return fail(EF_EINVAL, "ef_prob_exact_noalloc_dev: this call needs " + std::to_string(need) +
                                    " bytes of scratch, the fixed scratch holds " + std::to_string(kNoAllocBytes) +
                                    "; pass at most " + std::to_string(fit) + " bitstrings per call for this circuit");
@@ -1139,7 +1255,7 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
     unsigned char* base = nullptr;
     int rc = noalloc_base(&base);
     if (rc) return rc;
-    noalloc_layout(c, nb, !fp64_only, base, pl);
+    noalloc_layout(c, nb, !fp64_only, base, eb, tb);
 
     if (c->has_last_stream && c->last_stream != s) EF_CK(cudaStreamSynchronize(c->last_stream));
     c->last_stream = s;
@@ -1147,77 +1263,30 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
     c->stats = ef_stats{};
     c->last_mode = 1;
     c->last_fp64_list_pending = 0;
+    c->last_recomp = nullptr;
     c->timed = false;
     c->stats.logical_branch_dets = nb * (int64_t)std::ldexp(1.0, (int)c->cps.size());
     if (nb == 0) return EF_OK;
 
     ef::LaunchStats st;
-    int64_t sub_total = 0;
     for (int b = 0; b < c->nblocks; ++b) {
         HostBlock& B = c->blk[b];
         const size_t nn = (size_t)B.n * B.n;
-        EF_CK(cudaMemcpyAsync(pl.S0[b], B.S.data(), nn * sizeof(double2), cudaMemcpyHostToDevice, s));
-        EF_CK(copy_in(pl.cols[b], B.cols, s));
-        if (B.L > 0)
-            EF_CK(cudaMemcpyAsync(const_cast<double2*>(pl.blk[b].T), B.T.data() + nn, (size_t)B.L * nn * sizeof(double2),
-                                  cudaMemcpyHostToDevice, s));
-        EF_CK(copy_in(const_cast<uint32_t*>(pl.blk[b].F), B.F, s));
-        EF_CK(copy_in(const_cast<double*>(pl.blk[b].WLlo), B.WLlo, s));
-        EF_CK(copy_in(const_cast<double*>(pl.blk[b].WLhi), B.WLhi, s));
-        k_gather_columns<<<32, 128, 0, s>>>(pl.S0[b], pl.cols[b], B.n, B.eta, const_cast<double2*>(pl.blk[b].S0C));
+        const ef::ExactBlockDev& d = eb.blk[b];
+        EF_CK(copy_in_c(tb.S0[b], B.S.data(), nn, s));
+        EF_CK(copy_in(tb.cols[b], B.cols, s));
+        if (B.L > 0) EF_CK(copy_in_c(d.T, B.T.data() + nn, (size_t)B.L * nn, s));
+        EF_CK(copy_in(d.F, B.F, s));
+        EF_CK(copy_in_c(eb.Omega[b], B.Omega.data(), B.Omega.size(), s));
+        EF_CK(copy_in(eb.Omega32[b], B.Omega32, s));
+        EF_CK(copy_in(eb.sh[b], B.sh, s));
+        EF_CK(copy_in(eb.perm[b], B.perm, s));
+        EF_CK(copy_in(eb.goff[b], B.goff, s));
+        k_gather_columns<<<32, 128, 0, s>>>(tb.S0[b], tb.cols[b], B.n, B.eta, const_cast<double2*>(d.S0C));
         EF_CK(cudaGetLastError());
         st.launches += 1;
-        sub_total += (int64_t)1 << (B.k_loc + pl.blk[b].k_sh);
     }
-    EF_CK(copy_in(pl.WSlo, c->WSlo, s));
-    EF_CK(copy_in(pl.WShi, c->WShi, s));
-    c->last_sub_total = sub_total;
-
-    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_build_branches(pl.blk[b], !fp64_only, s, st));
-
-    ef::ExactCombineDev cm{};
-    cm.nblocks = c->nblocks;
-    cm.k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
-    cm.shlobits = c->shlobits;
-    cm.WSlo = pl.WSlo;
-    cm.WShi = pl.WShi;
-    cm.inactive0 = c->inactive[0];
-    cm.inactive1 = c->inactive[1];
-    for (int b = 0; b < c->nblocks; ++b) {
-        cm.mask[b][0] = c->blk[b].mask[0];
-        cm.mask[b][1] = c->blk[b].mask[1];
-        cm.eta[b] = c->blk[b].eta;
-        cm.c_log2[b] = c->blk[b].c_log2;
-        cm.k_loc[b] = c->blk[b].k_loc;
-        cm.part[b] = pl.blk[b].part;
-        cm.eta_max = std::max(cm.eta_max, c->blk[b].eta);
-    }
-    cm.tol = c->opt.tol;
-    cm.p_floor = c->p_floor;
-    const double K = c->opt.tile_override[1] > 0 ? 0.1 * c->opt.tile_override[1] : 3.0;
-    cm.err_coef = fp64_only ? 0.0 : K * std::ldexp(1.0, -24);
-
-    for (int b = 0; b < c->nblocks; ++b) {
-        const ef::ExactBlockDev& d = pl.blk[b];
-        if (fp64_only) {
-            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, nullptr, nullptr, nb, true, s, st));
-        } else if (d.eta <= ef::kMaxEtaThread) {
-            EF_CK(ef::launch_exact_lu_f32(d, d_bits, nb, s, st));
-        } else {
-            EF_CK(ef::launch_exact_lu_rows(d, d_bits, nb, nullptr, nullptr, nb, false, s, st));
-        }
-    }
-    // the scratch keeps the previous call's contents: the recompute list count starts at zero
-    EF_CK(cudaMemsetAsync(pl.count, 0, sizeof(int), s));
-    EF_CK(ef::launch_exact_combine(cm, d_bits, nb, nullptr, nullptr, d_out, d_err_out, autofix ? pl.list : nullptr,
-                                   autofix ? pl.count : nullptr, s, st));
-    if (autofix) {
-        for (int b = 0; b < c->nblocks; ++b)
-            EF_CK(ef::launch_exact_lu_rows(pl.blk[b], d_bits, nb, pl.list, pl.count, nb, true, s, st));
-        cm.err_coef = 0.0;
-        EF_CK(ef::launch_exact_combine(cm, d_bits, nb, pl.list, pl.count, d_out, d_err_out, nullptr, nullptr, s, st));
-    }
-    c->stats.kernel_launches = st.launches;
-    c->stats.executed_minor_lus = st.executed_lus;
-    return EF_OK;
+    EF_CK(copy_in_c(eb.WS, c->WS.data(), c->WS.size(), s));
+    EF_CK(copy_in(eb.WS32, c->WS32, s));
+    return run_exact(c, eb, d_bits, nb, d_out, d_err_out, s, st);
 }

@@ -3,16 +3,21 @@
 // The circuit's modes split into at most two independent blocks (modes joined
 // by Givens rotations; controlled-phase gates are diagonal and never join
 // them). For a trajectory x the mode matrix is block diagonal, so the minor's
-// determinant is the product of the blocks' minors, and each block's factor
-// depends only on the bits y of the gates touching that block. Per block:
+// determinant is the product of the blocks' minors. Inside a block the
+// trajectory enters only through its flip pattern: D_{x_j} = D_0 W_j with
+// W_j = diag(-1 on the gate's modes)^{x_j} (Section IV-B, Eqs. 15-16), so the
+// block's matrix is U(x) = T_L W_L(x) ... T_1 W_1(x) S_0 with W_l(x) the
+// product of the layer's W_j: only which modes flip in which layer matters.
+// Patterns form a GF(2) vector space; each block enumerates the 2^r patterns
+// once instead of the 2^{k_B} bit vectors, and the host folds the branch
+// weights w(x) onto patterns. Per block:
 //
-//   1. k_build_branches  : U_B(y)[:, C_B] = T_L W_L(y) ... T_1 W_1(y) S_0[:, C_B]
-//      for every sub-branch y (Section IV-B, Eq. 14 generalised: T_l is the
-//      passive segment times the layer's base phases, W_l(y) = diag(+-1)).
-//   2. k_exact_lu_*      : per (bitstring, chunk of sub-branches) the weighted
-//      sum of minors det U_B(y)[R_B(b), C_B] (Eq. 3), LU with partial pivoting.
-//   3. k_exact_combine   : amp(b) = sum_{y_sh} w_sh(y_sh) prod_B A_B(b, y_sh),
-//      p(b) = |amp(b)|^2, plus the FP32 path's per-result error estimate.
+//   1. k_build_branches : U_B(z)[:, C_B] for every pattern z (dense FP64 products);
+//   2. k_exact_lu_*     : det U_B(z)[R_B(b), C_B] (Eq. 3) for every (pattern, bitstring),
+//                         LU with partial pivoting, plus a rounding-error proxy;
+//   3. k_exact_combine  : amp(b) = sum_{x_sh} w_sh(x_sh) prod_B A_B(x_sh) with
+//                         A_B(x_sh) = sum_{z local} Omega_B(z) det_B(z ^ s_B(x_sh)),
+//                         p(b) = |amp|^2, and the FP32 path's error estimate.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,13 +36,13 @@ __global__ void __launch_bounds__(128) k_build_branches(ExactBlockDev B, int wan
     double2* bufA = smb;
     double2* bufB = smb + ne;
     int* sgn = reinterpret_cast<int*>(smb + 2 * ne);
-    const uint32_t ny = 1u << (B.k_loc + B.k_sh);
-    for (uint32_t y = blockIdx.x; y < ny; y += gridDim.x) {
+    const uint32_t ny = 1u << B.r;
+    for (uint32_t z = blockIdx.x; z < ny; z += gridDim.x) {
         double2* cur = bufA;
         double2* nxt = bufB;
         for (int e = threadIdx.x; e < ne; e += blockDim.x) cur[e] = B.S0C[e];
         for (int l = 0; l < B.L; ++l) {
-            for (int m = threadIdx.x; m < n; m += blockDim.x) sgn[m] = __popc(y & B.F[l * n + m]) & 1;
+            for (int m = threadIdx.x; m < n; m += blockDim.x) sgn[m] = __popc(z & B.F[l * n + m]) & 1;
             __syncthreads();
             const double2* T = B.T + (size_t)l * n * n;
             for (int e = threadIdx.x; e < ne; e += blockDim.x) {
@@ -61,11 +66,11 @@ __global__ void __launch_bounds__(128) k_build_branches(ExactBlockDev B, int wan
             nxt = tmp;
         }
         __syncthreads();
-        double2* o64 = B.M64 + (size_t)y * ne;
+        double2* o64 = B.M64 + (size_t)z * ne;
         for (int e = threadIdx.x; e < ne; e += blockDim.x) {
             const double2 v = cur[e];
             o64[e] = v;
-            if (want32) B.M32[(size_t)y * ne + e] = make_float2((float)v.x, (float)v.y);
+            if (want32) B.M32[(size_t)z * ne + e] = make_float2((float)v.x, (float)v.y);
         }
         __syncthreads();
     }
@@ -75,7 +80,7 @@ cudaError_t launch_build_branches(const ExactBlockDev& b, bool want32, cudaStrea
     const size_t smem = (size_t)2 * b.n * b.eta * sizeof(double2) + (size_t)b.n * sizeof(int);
     cudaError_t e = cudaFuncSetAttribute(k_build_branches, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const uint32_t ny = 1u << (b.k_loc + b.k_sh);
+    const uint32_t ny = 1u << b.r;
     const int grid = (int)std::min<uint32_t>(ny, 152u * 16u);
     k_build_branches<<<grid, 128, smem, s>>>(b, want32 ? 1 : 0);
     st.launches += 1;
@@ -83,9 +88,18 @@ cudaError_t launch_build_branches(const ExactBlockDev& b, bool want32, cudaStrea
 }
 
 // ---------------------------------------------------------------- 2a. FP32, thread per minor
-// Thread <-> bitstring; the CTA stages one chunk of 2^c_log2 branch matrices
-// (row stride ETA|1 float2 so that rows of one chunk fall in distinct banks)
-// and every thread walks the chunk, factoring its own minor in registers.
+// Thread <-> bitstring; the CTA stages one chunk of 2^c_log2 pattern matrices
+// (row stride ETA|1 float2 so that the rows of a matrix fall in distinct
+// banks) and every thread factors its own minor of each, in registers.
+
+int exact_f32_chunk_log2(int n, int eta, int r, int64_t nb) {
+    int cl = std::min(r, 5);
+    while (cl > 0 && ((size_t)1 << cl) * n * (size_t)(eta | 1) * sizeof(float2) > 48 * 1024) --cl;
+    // keep at least ~8 waves of 3 CTAs per SM
+    const int64_t tiles = (nb + 127) / 128;
+    while (cl > 0 && tiles * ((int64_t)1 << (r - cl)) < 152 * 3 * 8) --cl;
+    return cl;
+}
 
 template <int ETA>
 __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uint64_t* __restrict__ bits,
@@ -97,8 +111,6 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int rows[ETA];
     const bool ok = (b < nb) && decode_rows<ETA>(bits[2 * b], bits[2 * b + 1], B.mask0, B.mask1, rows);
-    const uint32_t locmask = (1u << B.k_loc) - 1u;
-    const uint32_t lomask = (1u << B.lobits) - 1u;
     for (int chunk = blockIdx.y; chunk < B.n_chunks; chunk += gridDim.y) {
         const float2* src = B.M32 + (size_t)chunk * Y * n * ETA;
         __syncthreads();
@@ -108,11 +120,10 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
         }
         __syncthreads();
         if (b >= nb) continue;
-        d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
-        if (ok) {
-            double ar = 0.0, ai = 0.0;
-            double ssum = 0.0, esum = 0.0;
-            for (int t = 0; t < Y; ++t) {
+        for (int t = 0; t < Y; ++t) {
+            const size_t z = (size_t)chunk * Y + t;
+            d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
+            if (ok) {
                 const float2* Mt = smM + (size_t)t * n * S;
                 float2 A[ETA][ETA];
 #pragma unroll
@@ -123,20 +134,10 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
                 }
                 float er2, zabs2;
                 const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
-                const uint32_t y = (uint32_t)chunk * (uint32_t)Y + (uint32_t)t;
-                const uint32_t yl = y & locmask;
-                const double wr = B.WLlo[yl & lomask] * B.WLhi[yl >> B.lobits];
-                const double2 wd = times_i_pow(make_double2(wr * (double)det.x, wr * (double)det.y), __popc(yl));
-                ar += wd.x;
-                ai += wd.y;
-                const double w2 = wr * wr;
-                const double d2 = (double)det.x * det.x + (double)det.y * det.y;
-                ssum = fma(w2, d2, ssum);
-                esum = fma(w2, fma(d2, (double)er2, (double)zabs2), esum);
+                res = make_d4((double)det.x, (double)det.y, (double)er2, (double)zabs2);
             }
-            res = make_d4(ar, ai, ssum, esum);
+            B.D[z * nb + b] = res;
         }
-        B.part[(size_t)chunk * nb + b] = res;
     }
 }
 
@@ -169,20 +170,65 @@ cudaError_t launch_exact_lu_f32(const ExactBlockDev& b, const uint64_t* bits, in
         default: return cudaErrorInvalidValue;
     }
     st.launches += 1;
-    st.executed_lus += nb * ((int64_t)b.n_chunks << b.c_log2);
+    st.executed_lus += nb * ((int64_t)1 << b.r);
     return e;
 }
 
-// ---------------------------------------------------------------- 2b. warp-row LU (FP64, or FP32 for large eta)
-// A group of G lanes handles one (bitstring, chunk) work item; lane r holds
-// row r of each minor. Work items are visited warp-uniformly in a grid-stride
-// loop; in list mode the bitstrings are list[0..*list_count) (the results the
-// FP32 path flagged) and partials go to [chunk][list position] with stride cap.
+// ---------------------------------------------------------------- 2b. FP64, thread per minor
+// Thread <-> (pattern, bitstring) work item, consecutive threads on
+// consecutive bitstrings of one pattern; the minor is gathered from the FP64
+// branch matrices in L2. Used for eta <= 8 (the FP64 pipe, not the register
+// file, bounds it; the compiler may keep part of the matrix in local memory).
+
+template <int ETA>
+__global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const uint64_t* __restrict__ bits,
+                                                       int64_t nb, const int* __restrict__ list,
+                                                       const int* __restrict__ list_count, int64_t stride) {
+    const int64_t count = list ? (int64_t)(*list_count) : nb;
+    const int64_t total = count << B.r;
+    const int n = B.n;
+    for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < total;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t z = item / count;
+        const int64_t pos = item - z * count;
+        const int64_t b = list ? (int64_t)list[pos] : pos;
+        int rows[ETA];
+        d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
+        if (decode_rows<ETA>(bits[2 * b], bits[2 * b + 1], B.mask0, B.mask1, rows)) {
+            const double2* Mz = B.M64 + (size_t)z * n * ETA;
+            double2 A[ETA][ETA];
+#pragma unroll
+            for (int i = 0; i < ETA; ++i)
+#pragma unroll
+                for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
+            double er2, zabs2;
+            const double2 det = lu_det_regs<double, ETA>(A, er2, zabs2);
+            res = make_d4(det.x, det.y, er2, zabs2);
+        }
+        B.D[(size_t)z * stride + pos] = res;
+    }
+}
+
+template <int ETA>
+static cudaError_t launch_f64t_eta(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, const int* list,
+                                   const int* list_count, int64_t stride, cudaStream_t s) {
+    const int64_t items = (list ? stride : nb) << b.r;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, 152 * 32));
+    k_exact_lu_f64t<ETA><<<(unsigned)blocks, 128, 0, s>>>(b, bits, nb, list, list_count, stride);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- 2c. warp-row LU (FP64, or FP32 for large eta)
+// A group of G lanes handles one (bitstring, chunk of patterns) work item;
+// lane r holds row r of each minor. Work items are visited warp-uniformly in
+// a grid-stride loop; in list mode the bitstrings are list[0..*list_count)
+// (the results the FP32 path flagged) and determinants go to
+// D[pattern][list position] (row stride `stride`).
 
 template <typename R, int G>
 __global__ void __launch_bounds__(256) k_exact_lu_rows(ExactBlockDev B, const uint64_t* __restrict__ bits,
                                                        int64_t nb, const int* __restrict__ list,
-                                                       const int* __restrict__ list_count, int64_t cap,
+                                                       const int* __restrict__ list_count, int64_t stride,
                                                        const cplx_t<R>* __restrict__ M) {
     using T = cplx_t<R>;
     const int lane = threadIdx.x & 31;
@@ -191,12 +237,9 @@ __global__ void __launch_bounds__(256) k_exact_lu_rows(ExactBlockDev B, const ui
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t count = list ? (int64_t)(*list_count) : nb;
-    const int64_t stride = list ? cap : nb;
+    const int Y = 1 << B.c_log2;
     const int64_t total = count * (int64_t)B.n_chunks;
     const int n = B.n, eta = B.eta;
-    const int Y = 1 << B.c_log2;
-    const uint32_t locmask = (1u << B.k_loc) - 1u;
-    const uint32_t lomask = (1u << B.lobits) - 1u;
     for (int64_t wbase = warp_global * GPW; wbase < total; wbase += nwarps * GPW) {
         const int64_t item = wbase + lane / G;
         const bool valid = item < total;
@@ -208,52 +251,42 @@ __global__ void __launch_bounds__(256) k_exact_lu_rows(ExactBlockDev B, const ui
             row_idx = nth_row(bits[2 * b], bits[2 * b + 1], B.mask0, B.mask1, r, cnt);
         }
         const bool ok = valid && (cnt == eta);
-        double ar = 0.0, ai = 0.0, ssum = 0.0, esum = 0.0;
         for (int t = 0; t < Y; ++t) {
-            const uint32_t y = (uint32_t)chunk * (uint32_t)Y + (uint32_t)t;
+            const size_t z = (size_t)chunk * Y + t;
             T rowv[G];
-            const T* src = M + ((size_t)y * n + (size_t)(row_idx < 0 ? 0 : row_idx)) * eta;
+            const T* src = M + (z * n + (size_t)(row_idx < 0 ? 0 : row_idx)) * eta;
             const bool live = ok && r < eta;
 #pragma unroll
             for (int j = 0; j < G; ++j) rowv[j] = (live && j < eta) ? src[j] : mk(R(0), R(0));
             R er2, zabs2;
             const T det = lu_det_rows<R, G>(rowv, r, eta, er2, zabs2);
-            const uint32_t yl = y & locmask;
-            const double wr = B.WLlo[yl & lomask] * B.WLhi[yl >> B.lobits];
-            const double2 wd = times_i_pow(make_double2(wr * (double)det.x, wr * (double)det.y), __popc(yl));
-            ar += wd.x;
-            ai += wd.y;
-            const double w2 = wr * wr;
-            const double d2 = (double)det.x * det.x + (double)det.y * det.y;
-            ssum = fma(w2, d2, ssum);
-            esum = fma(w2, fma(d2, (double)er2, (double)zabs2), esum);
+            if (valid && r == 0)
+                B.D[z * stride + pos] = ok ? make_d4((double)det.x, (double)det.y, (double)er2, (double)zabs2)
+                                           : make_d4(0.0, 0.0, 0.0, 0.0);
         }
-        if (valid && r == 0)
-            B.part[(size_t)chunk * stride + pos] = ok ? make_d4(ar, ai, ssum, esum) : make_d4(0, 0, 0, 0);
     }
 }
 
 template <typename R, int G>
 static cudaError_t launch_rows_g(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, const int* list,
-                                 const int* list_count, int64_t cap, const void* M, cudaStream_t s) {
-    const int64_t count = list ? cap : nb;
-    const int64_t items = count * (int64_t)b.n_chunks;
+                                 const int* list_count, int64_t stride, const void* M, cudaStream_t s) {
+    const int64_t items = (list ? stride : nb) * (int64_t)b.n_chunks;
     const int64_t warps = (items + (32 / G) - 1) / (32 / G);
     int64_t blocks = (warps + 7) / 8;
     blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
-    k_exact_lu_rows<R, G><<<(unsigned)blocks, 256, 0, s>>>(b, bits, nb, list, list_count, cap,
+    k_exact_lu_rows<R, G><<<(unsigned)blocks, 256, 0, s>>>(b, bits, nb, list, list_count, stride,
                                                           reinterpret_cast<const cplx_t<R>*>(M));
     return cudaGetLastError();
 }
 
 template <typename R>
 static cudaError_t launch_rows_r(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, const int* list,
-                                 const int* list_count, int64_t cap, const void* M, cudaStream_t s) {
-    if (b.eta <= 2) return launch_rows_g<R, 2>(b, bits, nb, list, list_count, cap, M, s);
-    if (b.eta <= 4) return launch_rows_g<R, 4>(b, bits, nb, list, list_count, cap, M, s);
-    if (b.eta <= 8) return launch_rows_g<R, 8>(b, bits, nb, list, list_count, cap, M, s);
-    if (b.eta <= 16) return launch_rows_g<R, 16>(b, bits, nb, list, list_count, cap, M, s);
-    return launch_rows_g<R, 32>(b, bits, nb, list, list_count, cap, M, s);
+                                 const int* list_count, int64_t stride, const void* M, cudaStream_t s) {
+    if (b.eta <= 2) return launch_rows_g<R, 2>(b, bits, nb, list, list_count, stride, M, s);
+    if (b.eta <= 4) return launch_rows_g<R, 4>(b, bits, nb, list, list_count, stride, M, s);
+    if (b.eta <= 8) return launch_rows_g<R, 8>(b, bits, nb, list, list_count, stride, M, s);
+    if (b.eta <= 16) return launch_rows_g<R, 16>(b, bits, nb, list, list_count, stride, M, s);
+    return launch_rows_g<R, 32>(b, bits, nb, list, list_count, stride, M, s);
 }
 
 cudaError_t launch_exact_lu_rows(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, const int* list,
@@ -263,93 +296,173 @@ cudaError_t launch_exact_lu_rows(const ExactBlockDev& b, const uint64_t* bits, i
     cudaError_t e = fp64 ? launch_rows_r<double>(b, bits, nb, list, list_count, cap, b.M64, s)
                          : launch_rows_r<float>(b, bits, nb, list, list_count, cap, b.M32, s);
     st.launches += 1;
-    if (!list) st.executed_lus += nb * ((int64_t)b.n_chunks << b.c_log2);
+    if (!list) st.executed_lus += nb * ((int64_t)1 << b.r);
+    return e;
+}
+
+cudaError_t launch_exact_lu_f64(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, const int* list,
+                                const int* list_count, int64_t cap, cudaStream_t s, LaunchStats& st) {
+    if ((list ? cap : nb) <= 0) return cudaSuccess;
+    cudaError_t e;
+    switch (b.eta) {
+        case 1: e = launch_f64t_eta<1>(b, bits, nb, list, list_count, cap, s); break;
+        case 2: e = launch_f64t_eta<2>(b, bits, nb, list, list_count, cap, s); break;
+        case 3: e = launch_f64t_eta<3>(b, bits, nb, list, list_count, cap, s); break;
+        case 4: e = launch_f64t_eta<4>(b, bits, nb, list, list_count, cap, s); break;
+        case 5: e = launch_f64t_eta<5>(b, bits, nb, list, list_count, cap, s); break;
+        case 6: e = launch_f64t_eta<6>(b, bits, nb, list, list_count, cap, s); break;
+        case 7: e = launch_f64t_eta<7>(b, bits, nb, list, list_count, cap, s); break;
+        case 8: e = launch_f64t_eta<8>(b, bits, nb, list, list_count, cap, s); break;
+        default: return launch_exact_lu_rows(b, bits, nb, list, list_count, cap, true, s, st);
+    }
+    st.launches += 1;
+    if (!list) st.executed_lus += nb * ((int64_t)1 << b.r);
     return e;
 }
 
 // ---------------------------------------------------------------- 3. combine
+// One CTA per bitstring. Phase 1 (FP64): A_B(x_sh) for every shared bit
+// vector and amp = sum w_sh A_0 A_1. Phase 2 (FP32 path only): the error
+// estimate. Each determinant det_B(z) enters amp with the coefficient
+// C_B(z) = sum_{x_sh} w_sh(x_sh) Omega_B(z ^ s_B(x_sh)) A_other(x_sh), and
+// rounding errors of different determinants are independent, so
+// Var(d amp) = (K u)^2 sum_{B,z} |C_B(z)|^2 (|det|^2 er2 + zabs2).
+
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int off = NT / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
 
 __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const uint64_t* __restrict__ bits,
-                                                       int64_t nb, const int* __restrict__ list,
-                                                       const int* __restrict__ list_count, int64_t stride,
-                                                       double* __restrict__ out, double* __restrict__ err,
-                                                       int* __restrict__ append_list, int* __restrict__ append_count) {
+                                                       int64_t nb, int64_t stride, const int* __restrict__ list,
+                                                       const int* __restrict__ list_count, double* __restrict__ out,
+                                                       double* __restrict__ err, int* __restrict__ append_list,
+                                                       int* __restrict__ append_count) {
+    constexpr int NT = 256;
+    extern __shared__ float2 smA32[];  // FP32 copies of A_0[2^k_sh], A_1[2^k_sh] for the error estimate
+    __shared__ double red[NT];
+    const int tid = threadIdx.x;
     const int64_t count = list ? (int64_t)(*list_count) : nb;
-    for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < count;
-         pos += (int64_t)gridDim.x * blockDim.x) {
+    if (list && C.recomputed_total && blockIdx.x == 0 && tid == 0) atomicAdd(C.recomputed_total, (int)count);
+    const int nsh = 1 << C.k_sh;
+    const bool want_err = C.err_coef > 0.0;
+    for (int64_t pos = blockIdx.x; pos < count; pos += gridDim.x) {
         const int64_t b = list ? (int64_t)list[pos] : pos;
         const uint64_t w0 = bits[2 * b], w1 = bits[2 * b + 1];
         bool ok = ((w0 & C.inactive0) == 0) && ((w1 & C.inactive1) == 0);
         for (int B = 0; B < C.nblocks; ++B)
             ok = ok && (__popcll(w0 & C.mask[B][0]) + __popcll(w1 & C.mask[B][1]) == C.eta[B]);
-        double p = 0.0, e = 0.0;
-        if (ok) {
-            double ar = 0.0, ai = 0.0, S = 0.0, E = 0.0;
-            if (C.nblocks == 0) {
-                ar = 1.0;
-                S = 1.0;
-            } else if (C.nblocks == 1) {
-                const int nch = 1 << (C.k_loc[0] + C.k_sh - C.c_log2[0]);
-                for (int c = 0; c < nch; ++c) {
-                    const d4 v = C.part[0][(size_t)c * stride + pos];
-                    ar += v.x;
-                    ai += v.y;
-                    S += v.z;
-                    E += v.w;
-                }
-            } else {
-                const int nys = 1 << C.k_sh;
-                const int cpy0 = 1 << (C.k_loc[0] - C.c_log2[0]);
-                const int cpy1 = 1 << (C.k_loc[1] - C.c_log2[1]);
-                const uint32_t lomask = (1u << C.shlobits) - 1u;
-                for (int ys = 0; ys < nys; ++ys) {
-                    double a0r = 0, a0i = 0, s0 = 0, e0 = 0, a1r = 0, a1i = 0, s1 = 0, e1 = 0;
-                    for (int c = ys * cpy0; c < (ys + 1) * cpy0; ++c) {
-                        const d4 v = C.part[0][(size_t)c * stride + pos];
-                        a0r += v.x; a0i += v.y; s0 += v.z; e0 += v.w;
-                    }
-                    for (int c = ys * cpy1; c < (ys + 1) * cpy1; ++c) {
-                        const d4 v = C.part[1][(size_t)c * stride + pos];
-                        a1r += v.x; a1i += v.y; s1 += v.z; e1 += v.w;
-                    }
-                    const double wr = C.WSlo[ys & lomask] * C.WShi[(uint32_t)ys >> C.shlobits];
-                    const double2 prod = times_i_pow(make_double2(a0r * a1r - a0i * a1i, a0r * a1i + a0i * a1r),
-                                                     __popc((unsigned)ys));
-                    ar = fma(wr, prod.x, ar);
-                    ai = fma(wr, prod.y, ai);
-                    const double w2 = wr * wr;
-                    S = fma(w2, s0 * s1, S);
-                    E = fma(w2, e0 * s1 + s0 * e1, E);
-                }
+        if (!ok) {
+            if (tid == 0) {
+                out[b] = 0.0;
+                if (err && !list) err[b] = 0.0;
             }
-            p = ar * ar + ai * ai;
-            // rounding errors of different minors are independent: the FP32
-            // amplitude error is estimated in quadrature, |d amp| ~ K eta u sqrt(2 E)
-            const double dabs = 2.0 * sqrt(p) * C.err_coef * sqrt(2.0 * E);
-            e = dabs / fmax(p, C.p_floor);
+            continue;
         }
-        out[b] = p;
-        if (list) {
-            if (err) err[b] = -fabs(err[b]);
+        double ar = 0.0, ai = 0.0, var = 0.0;
+        if (C.nblocks == 0) {
+            ar = tid == 0 ? 1.0 : 0.0;
+        } else if (C.nblocks == 1) {
+            // amp = sum_z Omega(z) det(z); C(z) = Omega(z)
+            const int nz = 1 << C.r[0];
+            for (int z = tid; z < nz; z += NT) {
+                const d4 v = C.D[0][(size_t)z * stride + pos];
+                const double2 w = C.Omega[0][z];
+                ar = fma(w.x, v.x, fma(-w.y, v.y, ar));
+                ai = fma(w.x, v.y, fma(w.y, v.x, ai));
+                if (want_err) var = fma(w.x * w.x + w.y * w.y, fma(v.x * v.x + v.y * v.y, v.z, v.w), var);
+            }
         } else {
-            if (err) err[b] = e;
-            if (append_list && e > C.tol) {
-                const int idx = atomicAdd(append_count, 1);
-                append_list[idx] = (int)b;
+            const int nl0 = 1 << C.r_loc[0], nl1 = 1 << C.r_loc[1];
+            for (int xs = tid; xs < nsh; xs += NT) {
+                double2 a[2];
+                for (int B = 0; B < 2; ++B) {
+                    const uint32_t sB = C.s[B][xs];
+                    const int nl = B == 0 ? nl0 : nl1;
+                    double sx = 0.0, sy = 0.0;
+                    for (int zl = 0; zl < nl; ++zl) {
+                        const d4 v = C.D[B][(size_t)(zl ^ sB) * stride + pos];
+                        const double2 w = C.Omega[B][zl];
+                        sx = fma(w.x, v.x, fma(-w.y, v.y, sx));
+                        sy = fma(w.x, v.y, fma(w.y, v.x, sy));
+                    }
+                    a[B] = make_double2(sx, sy);
+                    if (want_err)
+                        smA32[B * nsh + xs] = make_float2((float)sx, (float)sy);
+                }
+                const double2 t = cmul_d(C.WS[xs], cmul_d(a[0], a[1]));
+                ar += t.x;
+                ai += t.y;
+            }
+            if (want_err) {
+                // the estimate needs no FP64: coefficients in FP32
+                __syncthreads();
+                for (int B = 0; B < 2; ++B) {
+                    const int nz = 1 << C.r[B];
+                    const uint32_t lmask = (1u << C.r_loc[B]) - 1u;
+                    const float2* Aoth = smA32 + (1 - B) * nsh;
+                    for (int z = tid; z < nz; z += NT) {
+                        const uint32_t h = (uint32_t)z >> C.r_loc[B];
+                        float cx = 0.f, cy = 0.f;
+                        for (uint32_t g = C.goff[B][h]; g < C.goff[B][h + 1]; ++g) {
+                            const uint32_t xs = C.perm[B][g];
+                            const uint32_t zl = ((uint32_t)z ^ C.s[B][xs]) & lmask;
+                            const float2 t = cmul(C.WS32[xs], cmul(C.Omega32[B][zl], Aoth[xs]));
+                            cx += t.x;
+                            cy += t.y;
+                        }
+                        const d4 v = C.D[B][(size_t)z * stride + pos];
+                        const double c2 = (double)cx * cx + (double)cy * cy;
+                        var = fma(c2, fma(v.x * v.x + v.y * v.y, v.z, v.w), var);
+                    }
+                }
             }
         }
+        ar = block_sum<NT>(ar, red);
+        ai = block_sum<NT>(ai, red);
+        if (want_err) var = block_sum<NT>(var, red);
+        if (tid == 0) {
+            const double p = ar * ar + ai * ai;
+            const double dabs = 2.0 * sqrt(p) * C.err_coef * sqrt(var);
+            const double e = dabs / fmax(p, C.p_floor);
+            out[b] = p;
+            if (list) {
+                if (err) err[b] = -fabs(err[b]);
+            } else {
+                if (err) err[b] = e;
+                if (append_list && e > C.tol) {
+                    const int idx = atomicAdd(append_count, 1);
+                    append_list[idx] = (int)b;
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
-cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits, int64_t nb, const int* list,
-                                 const int* list_count, double* out, double* err, int* append_list,
+cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits, int64_t nb, int64_t stride,
+                                 const int* list, const int* list_count, double* out, double* err, int* append_list,
                                  int* append_count, cudaStream_t s, LaunchStats& st) {
     if (nb <= 0) return cudaSuccess;
-    int64_t blocks = (nb + 255) / 256;
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 32));
-    // in list mode the partial stride is the list capacity (= nb)
-    k_exact_combine<<<(unsigned)blocks, 256, 0, s>>>(c, bits, nb, list, list_count, nb, out, err, append_list,
-                                                     append_count);
+    const size_t smem = (size_t)2 * ((size_t)1 << c.k_sh) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_exact_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, 152 * 16));
+    k_exact_combine<<<(unsigned)blocks, 256, smem, s>>>(c, bits, nb, stride, list, list_count, out, err, append_list,
+                                                        append_count);
     st.launches += 1;
     return cudaGetLastError();
 }

@@ -21,46 +21,53 @@ constexpr int kMaxEtaThread = 10;  // FP32 thread-per-minor LU (registers)
 constexpr int kMaxApproxEta = 8;   // Raw Estimate, thread per trajectory
 constexpr int kMaxApproxLayers = 8;
 constexpr int kMaxApproxStored = 64;  // rank-one columns kept per trajectory
-constexpr int kMaxExactSubBits = 24;  // 2^24 sub-branches per block
+constexpr int kMaxExactPatternBits = 22;  // 2^22 flip patterns per block
+constexpr int kMaxExactLocalBits = 22;    // local gates per block
+constexpr int kMaxExactSharedBits = 12;   // gates shared by the two blocks
 
 // ---------------------------------------------------------------- Exact mode
 
-// One independent mode block of the Exact path. Sub-branch y of the block
-// holds the bits of the controlled-phase gates that touch it: bits
-// [0, k_loc) for gates local to the block, [k_loc, k_loc + k_sh) for gates
-// shared with the other block.
+// One independent mode block of the Exact path. A trajectory's minor in the
+// block depends on the controlled-phase bits only through its flip pattern
+// (which local modes change sign in which layer), a GF(2)-linear function of
+// the bits. The r basis patterns span every pattern that occurs; pattern z
+// (r bits, coordinates in that basis) flips mode i of layer l iff
+// popcount(z & F[l*n + i]) is odd. The first r_loc basis patterns span the
+// patterns of the block's local gates.
 struct ExactBlockDev {
     int n, eta, L;          // modes, particles, diagonal layers in this block
-    int k_loc, k_sh;        // sub-branch bits
-    int c_log2;             // FP32 kernel: log2 sub-branches per chunk
-    int lobits;             // weight table split of the local bits
+    int r, r_loc;           // pattern rank, rank of the local gates' patterns
+    int c_log2;             // patterns per chunk of the FP32 kernel (log2)
+    int n_chunks;           // 2^(r - c_log2)
     uint64_t mask0, mask1;  // global modes of the block
     const double2* S0C;     // n x eta: first segment restricted to the occupied columns
     const double2* T;       // L x n x n: T_l = S_l diag(base phases of layer l)
-    const uint32_t* F;      // L x n: flip masks over y bits, per layer and local mode
-    const double* WLlo;     // 2^lobits
-    const double* WLhi;     // 2^(k_loc - lobits)
-    double2* M64;           // 2^(k_loc+k_sh) x n x eta branch matrices (FP64)
+    const uint32_t* F;      // L x n: flip masks over pattern bits
+    double2* M64;           // 2^r x n x eta branch matrices (FP64)
     float2* M32;            // same, FP32 (may be null)
-    d4* part;               // [n_chunks][count]: (re, im, S, E) per chunk
-    int n_chunks;           // 2^(k_loc + k_sh - c_log2)
+    d4* D;                  // [2^r][stride]: (det re, det im, er2, zabs2) per (pattern, bitstring)
 };
 
+// amp(b) = sum_{x_sh} WS[x_sh] prod_B A_B(x_sh),
+// A_B(x_sh) = sum_{z < 2^r_loc} Omega_B[z] det_B(z ^ s_B[x_sh]).
 struct ExactCombineDev {
     int nblocks;
-    int k_sh;
-    int shlobits;
-    const double* WSlo;
-    const double* WShi;
+    int k_sh;                       // bits of the gates shared by the two blocks
     uint64_t inactive0, inactive1;  // modes outside every active block (must be empty)
     uint64_t mask[kMaxBlocks][2];
     int eta[kMaxBlocks];
-    int c_log2[kMaxBlocks];
-    int k_loc[kMaxBlocks];
-    const d4* part[kMaxBlocks];
-    int eta_max;
-    double err_coef;  // K * eta_max * u32 (FP32 path), 0 for FP64
+    int r[kMaxBlocks], r_loc[kMaxBlocks];
+    const d4* D[kMaxBlocks];
+    const double2* Omega[kMaxBlocks];  // 2^r_loc pattern weights of the local gates
+    const uint32_t* s[kMaxBlocks];     // 2^k_sh: pattern of the shared bits
+    const uint32_t* perm[kMaxBlocks];  // shared bit patterns x_sh grouped by s >> r_loc
+    const uint32_t* goff[kMaxBlocks];  // 2^(r - r_loc) + 1 group offsets
+    const double2* WS;                 // 2^k_sh weights of the shared gates
+    const float2* Omega32[kMaxBlocks]; // FP32 copies for the error estimate
+    const float2* WS32;
+    double err_coef;                   // K u32 (FP32 path), 0 for FP64
     double tol, p_floor;
+    int* recomputed_total;             // list mode: accumulates the list sizes
 };
 
 // ---------------------------------------------------------------- Raw Estimate
@@ -102,10 +109,16 @@ struct LaunchStats {
 cudaError_t launch_build_branches(const ExactBlockDev& b, bool want32, cudaStream_t s, LaunchStats& st);
 cudaError_t launch_exact_lu_f32(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
                                 cudaStream_t s, LaunchStats& st);
+// largest pattern count (log2) a chunk of the FP32 kernel can stage in shared memory
+int exact_f32_chunk_log2(int n, int eta, int r, int64_t nb);
+// FP64 minors; thread per minor for eta <= 8, warp-row above
+cudaError_t launch_exact_lu_f64(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
+                                const int* list, const int* list_count, int64_t cap,
+                                cudaStream_t s, LaunchStats& st);
 cudaError_t launch_exact_lu_rows(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
                                  const int* list, const int* list_count, int64_t cap,
                                  bool fp64, cudaStream_t s, LaunchStats& st);
-cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits, int64_t nb,
+cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits, int64_t nb, int64_t stride,
                                  const int* list, const int* list_count, double* out, double* err,
                                  int* append_list, int* append_count, cudaStream_t s, LaunchStats& st);
 cudaError_t launch_approx(const ApproxDev& a, const uint64_t* bits, int64_t nb, bool fp64,
