@@ -94,6 +94,8 @@ struct HostBlock {
     std::vector<int> modes;  // local -> global
     std::vector<int> cols;   // occupied local modes
     std::vector<std::vector<int>> layers;  // cphase indices per layer (1..L -> [0..L-1])
+    std::vector<std::vector<int>> seg_gates;  // gate indices of segment l (0..L), in circuit order
+    std::vector<int> local_of;                // global mode -> local index (-1 outside)
     std::vector<cd> S;       // (L+1) n x n segments
     std::vector<cd> T;       // (L+1) n x n: T_0 = S_0, T_l = S_l diag(D_l0)
     // Exact
@@ -105,15 +107,17 @@ struct HostBlock {
     std::vector<float2> Omega32;   // FP32 copy (error estimate)
     std::vector<uint32_t> sh;      // 2^k_sh: pattern of each shared bit vector
     std::vector<uint32_t> perm, goff;  // shared bit vectors grouped by pattern >> r_loc
+    std::vector<uint32_t> coord;       // pattern coordinates of the local, then shared gates
     int c_log2 = 0;
     // Raw Estimate
     std::vector<cd> P;   // tri(L) x n x n
     std::vector<cd> RC;  // L x n x eta
     // device
     DBuf dS0C, dT, dF, dOmega, dOmega32, dSh, dPerm, dGoff, dM64, dM32, dD, dP64, dP32, dRC64, dRC32, dCols;
+    DBuf dCot, dEbar, dTbar, dSbar, dSumT, dSumS, dSumE;
     void release() {
         for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dSh, &dPerm, &dGoff, &dM64, &dM32, &dD, &dP64, &dP32, &dRC64,
-                        &dRC32, &dCols})
+                        &dRC32, &dCols, &dCot, &dEbar, &dTbar, &dSbar, &dSumT, &dSumS, &dSumE})
             b->release();
     }
 };
@@ -153,7 +157,7 @@ struct ef_circuit {
     double R0 = 1.0;
 
     bool dirty = true;
-    DBuf dWS, dWS32, dList, dListCount, dRecomp, dBits, dOut, dErr, dGradP, dGrad;
+    DBuf dWS, dWS32, dList, dListCount, dRecomp, dBits, dOut, dErr, dGradP, dGrad, dPbar, dSumP;
     DBuf daT, daq, dalayer, damodes, daPart, dCounters;
     cudaStream_t own_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -168,7 +172,7 @@ struct ef_circuit {
 
     ~ef_circuit() {
         for (int b = 0; b < ef::kMaxBlocks; ++b) blk[b].release();
-        for (DBuf* d : {&dWS, &dWS32, &dList, &dListCount, &dRecomp, &dBits, &dOut, &dErr, &dGradP, &dGrad, &daT,
+        for (DBuf* d : {&dWS, &dWS32, &dList, &dListCount, &dRecomp, &dBits, &dOut, &dErr, &dGradP, &dGrad, &dPbar, &dSumP, &daT,
                         &daq, &dalayer, &damodes, &daPart, &dCounters})
             d->release();
         if (ev0) cudaEventDestroy(ev0);
@@ -298,18 +302,22 @@ int prepare(ef_circuit* c) {
         };
         std::vector<std::vector<cd>> segs;
         B.layers.clear();
+        B.seg_gates.clear();
         std::vector<cd> seg = eye();
+        std::vector<int> segg;  // gates of the current segment, in order
         bool in_layer = false;
         std::vector<int> cur;
         int j = 0;
         std::vector<int> layer_of_cp(k, 0);
         for (const ef_gate& g : c->gates) {
+            const int gi = (int)(&g - c->gates.data());
             if (g.kind == EF_CPHASE) {
                 const CP& cp = c->cps[j];
                 const bool touches = cp.blk_p == b || cp.blk_q == b;
                 if (touches) {
                     if (!in_layer) {
                         segs.push_back(seg);
+                        B.seg_gates.push_back(segg);
                         in_layer = true;
                         cur.clear();
                     }
@@ -324,7 +332,9 @@ int prepare(ef_circuit* c) {
                 B.layers.push_back(cur);
                 in_layer = false;
                 seg = eye();
+                segg.clear();
             }
+            segg.push_back(gi);
             const int lp = local_of[g.p];
             if (g.kind == EF_GIVENS) {
                 const int lq = local_of[g.q];
@@ -344,8 +354,10 @@ int prepare(ef_circuit* c) {
         if (in_layer) {
             B.layers.push_back(cur);
             seg = eye();
+            segg.clear();
         }
         segs.push_back(seg);
+        B.seg_gates.push_back(segg);
         B.L = (int)B.layers.size();
         const int L = B.L;
         const size_t nn = (size_t)nb_ * nb_;
@@ -429,6 +441,8 @@ int prepare(ef_circuit* c) {
             if ((int)gi + 1 == B.k_loc) B.r_loc = (int)basis.size();
         }
         B.r = (int)basis.size();
+        B.coord = coord;
+        B.local_of = local_of;
         if (too_many || B.k_loc > ef::kMaxExactLocalBits || (c->nblocks == 2 && k_sh > ef::kMaxExactSharedBits)) {
             c->exact_ok = false;
             c->exact_why = "Exact mode: a mode block needs more than 2^" + std::to_string(ef::kMaxExactPatternBits) +
@@ -832,6 +846,251 @@ int exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out, 
     return run_exact(c, eb, d_bits, nb, d_out, d_err, s, st);
 }
 
+// ------------------------------------------------------------------ adjoint (host part)
+
+// Chain rule from the device cotangents to the angle vector.
+//   tbar[b][l]: d L / d T_{l+1} (n x n), sbar[b]: d L / d S_0[:, C] (n x eta),
+//   ebar[b]: d L / d Omega_b(z_local), pbar: d L / d w_sh(x_sh); all bilinear
+//   (dL = Re sum cot * d value).
+void grad_finish(const ef_circuit* c, const std::vector<std::vector<cd>>& tbar, const std::vector<std::vector<cd>>& sbar,
+                 const std::vector<std::vector<cd>>& ebar, const std::vector<cd>& pbar, std::vector<double>& grad) {
+    const cd I(0.0, 1.0);
+    static const cd ipow[4] = {cd(1, 0), cd(0, 1), cd(-1, 0), cd(0, -1)};
+    std::vector<int64_t> aidx(c->gates.size());
+    int64_t na = 0;
+    for (size_t gi = 0; gi < c->gates.size(); ++gi) {
+        aidx[gi] = na;
+        na += c->gates[gi].kind == EF_GIVENS ? 2 : 1;
+    }
+    grad.assign(na, 0.0);
+    // weights: w(y) = i^|y| prod_t (y_t ? s_t : c_t), ds/dtheta = c/4, dc/dtheta = -s/4
+    auto weight_grads = [&](const std::vector<int>& gates, const std::vector<uint32_t>& coord, int coff,
+                            const std::vector<cd>& cot, bool by_pattern) {
+        const int kk = (int)gates.size();
+        if (kk == 0) return;
+        std::vector<double> pre(kk + 1), suf(kk + 1);
+        for (uint64_t y = 0; y < (1ull << kk); ++y) {
+            uint32_t z = 0;
+            pre[0] = 1.0;
+            for (int t = 0; t < kk; ++t) {
+                const CP& cp = c->cps[gates[t]];
+                const bool bit = (y >> t) & 1ull;
+                if (bit && by_pattern) z ^= coord[coff + t];
+                pre[t + 1] = pre[t] * (bit ? cp.s : cp.c);
+            }
+            suf[kk] = 1.0;
+            for (int t = kk - 1; t >= 0; --t) {
+                const CP& cp = c->cps[gates[t]];
+                suf[t] = suf[t + 1] * (((y >> t) & 1ull) ? cp.s : cp.c);
+            }
+            const cd e = cot[by_pattern ? z : (uint32_t)y] * ipow[__builtin_popcountll(y) & 3];
+            for (int t = 0; t < kk; ++t) {
+                const CP& cp = c->cps[gates[t]];
+                const double dfac = ((y >> t) & 1ull) ? 0.25 * cp.c : -0.25 * cp.s;
+                grad[aidx[cp.gate]] += (e * (pre[t] * suf[t + 1] * dfac)).real();
+            }
+        }
+    };
+    for (int b = 0; b < c->nblocks; ++b) weight_grads(c->blk[b].local_gates, c->blk[b].coord, 0, ebar[b], true);
+    if (c->nblocks == 2) weight_grads(c->shared_gates, {}, 0, pbar, false);
+
+    for (int b = 0; b < c->nblocks; ++b) {
+        const HostBlock& B = c->blk[b];
+        const int n = B.n;
+        const size_t nn = (size_t)n * n;
+        std::vector<std::vector<cd>> Sbar(B.L + 1, std::vector<cd>(nn, cd(0, 0)));
+        for (int i = 0; i < n; ++i)
+            for (int cc = 0; cc < B.eta; ++cc) Sbar[0][(size_t)i * n + B.cols[cc]] = sbar[b][(size_t)i * B.eta + cc];
+        for (int l = 1; l <= B.L; ++l) {
+            std::vector<cd> d(n, cd(1, 0));
+            for (int jj : B.layers[l - 1]) {
+                const CP& cp = c->cps[jj];
+                const cd ph = std::polar(1.0, 0.5 * cp.theta);
+                if (cp.blk_p == b) d[B.local_of[cp.p]] *= ph;
+                if (cp.blk_q == b) d[B.local_of[cp.q]] *= ph;
+            }
+            const cd* Tb = &tbar[b][(size_t)(l - 1) * nn];
+            const cd* S = &B.S[(size_t)l * nn];
+            std::vector<cd> dbar(n, cd(0, 0));
+            for (int i = 0; i < n; ++i)
+                for (int m = 0; m < n; ++m) {
+                    dbar[m] += Tb[(size_t)i * n + m] * S[(size_t)i * n + m];
+                    Sbar[l][(size_t)i * n + m] = Tb[(size_t)i * n + m] * d[m];
+                }
+            for (int jj : B.layers[l - 1]) {
+                const CP& cp = c->cps[jj];
+                for (int side = 0; side < 2; ++side) {
+                    const int mode = side ? cp.q : cp.p;
+                    if ((side ? cp.blk_q : cp.blk_p) != b) continue;
+                    const int m = B.local_of[mode];
+                    grad[aidx[cp.gate]] += (dbar[m] * (0.5 * I) * d[m]).real();
+                }
+            }
+        }
+        // segments S_l = G_K ... G_1: dL/dG_k = (G_K..G_{k+1})^T Sbar (G_{k-1}..G_1)^T
+        for (int l = 0; l <= B.L; ++l) {
+            std::vector<cd> M = Sbar[l];
+            std::vector<cd> R(B.S.begin() + (size_t)l * nn, B.S.begin() + (size_t)(l + 1) * nn);
+            const std::vector<int>& seq = B.seg_gates[l];
+            for (int kk = (int)seq.size() - 1; kk >= 0; --kk) {
+                const ef_gate& g = c->gates[seq[kk]];
+                const int lp = B.local_of[g.p];
+                if (g.kind == EF_GIVENS) {
+                    const int lq = B.local_of[g.q];
+                    const double ct = std::cos(g.theta), st = std::sin(g.theta);
+                    const cd e = std::polar(1.0, g.phi), em = std::polar(1.0, -g.phi);
+                    const cd G[2][2] = {{ct, -e * st}, {em * st, ct}};
+                    const cd dT[2][2] = {{-st, -e * ct}, {em * ct, -st}};
+                    const cd dP[2][2] = {{0.0, -I * e * st}, {-I * em * st, 0.0}};
+                    for (int col = 0; col < n; ++col) {
+                        const cd a = R[(size_t)lp * n + col], bb = R[(size_t)lq * n + col];
+                        R[(size_t)lp * n + col] = std::conj(G[0][0]) * a + std::conj(G[1][0]) * bb;
+                        R[(size_t)lq * n + col] = std::conj(G[0][1]) * a + std::conj(G[1][1]) * bb;
+                    }
+                    const int ix[2] = {lp, lq};
+                    cd Gb[2][2];
+                    for (int a = 0; a < 2; ++a)
+                        for (int bb = 0; bb < 2; ++bb) {
+                            cd acc = 0;
+                            for (int col = 0; col < n; ++col) acc += M[(size_t)ix[a] * n + col] * R[(size_t)ix[bb] * n + col];
+                            Gb[a][bb] = acc;
+                        }
+                    double gt = 0.0, gp = 0.0;
+                    for (int a = 0; a < 2; ++a)
+                        for (int bb = 0; bb < 2; ++bb) {
+                            gt += (Gb[a][bb] * dT[a][bb]).real();
+                            gp += (Gb[a][bb] * dP[a][bb]).real();
+                        }
+                    grad[aidx[seq[kk]]] += gt;
+                    grad[aidx[seq[kk]] + 1] += gp;
+                    for (int col = 0; col < n; ++col) {
+                        const cd a = M[(size_t)lp * n + col], bb = M[(size_t)lq * n + col];
+                        M[(size_t)lp * n + col] = G[0][0] * a + G[1][0] * bb;
+                        M[(size_t)lq * n + col] = G[0][1] * a + G[1][1] * bb;
+                    }
+                } else {  // PHASE
+                    const cd e = std::polar(1.0, g.phi);
+                    for (int col = 0; col < n; ++col) R[(size_t)lp * n + col] *= std::conj(e);
+                    cd acc = 0;
+                    for (int col = 0; col < n; ++col) acc += M[(size_t)lp * n + col] * R[(size_t)lp * n + col];
+                    grad[aidx[seq[kk]]] += (acc * I * e).real();
+                    for (int col = 0; col < n; ++col) M[(size_t)lp * n + col] *= e;
+                }
+            }
+        }
+    }
+}
+
+int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_grad_p, double* d_out_p,
+             std::vector<double>& grad, cudaStream_t s) {
+    if (!c->exact_ok) return fail(EF_EUNSUPPORTED, c->exact_why);
+    for (int b = 0; b < c->nblocks; ++b) {
+        const HostBlock& B = c->blk[b];
+        if (B.eta > 8 || B.n > 64 || ef::grad_minors_smem(B.n, B.eta, B.L) > 227 * 1024)
+            return fail(EF_EUNSUPPORTED, "ef_prob_grad: supports mode blocks of at most 64 modes and 8 particles "
+                                         "(and layers x modes x particles within shared memory)");
+    }
+    int rc = begin_call(c, s, 3);
+    if (rc) return rc;
+    int64_t na = 0;
+    for (const ef_gate& g : c->gates) na += g.kind == EF_GIVENS ? 2 : 1;
+    grad.assign(na, 0.0);
+    c->stats.logical_branch_dets = nb * (int64_t)std::ldexp(1.0, (int)c->cps.size());
+    if (nb == 0) return EF_OK;
+    ef::LaunchStats st;
+    const int ksh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
+    size_t need = 0;
+    for (int b = 0; b < c->nblocks; ++b) {
+        const HostBlock& B = c->blk[b];
+        const size_t ny = (size_t)1 << B.r;
+        need += ny * (size_t)nb * (sizeof(ef::d4) + sizeof(double2)) + (size_t)nb * ((size_t)1 << B.r_loc) * 16 +
+                ny * ((size_t)B.L * B.n * B.n + (size_t)B.n * B.eta) * 16;
+    }
+    need += (size_t)nb * ((size_t)1 << ksh) * 16;
+    if (need > ((size_t)24 << 30))
+        return fail(EF_EUNSUPPORTED, "ef_prob_grad: the call needs " + std::to_string(need >> 20) +
+                                         " MiB of device workspace; split the bitstrings into smaller calls");
+    ef::GradDev g{};
+    ef::ExactCombineDev& cm = g.cm;
+    cm.nblocks = c->nblocks;
+    cm.k_sh = ksh;
+    cm.inactive0 = c->inactive[0];
+    cm.inactive1 = c->inactive[1];
+    cm.WS = c->dWS.as<double2>();
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        const size_t ny = (size_t)1 << B.r;
+        const size_t ne = (size_t)B.n * B.eta;
+        EF_CK(B.dM64.ensure(ny * ne * sizeof(double2)));
+        EF_CK(B.dD.ensure(ny * (size_t)nb * sizeof(ef::d4)));
+        EF_CK(B.dCot.ensure(ny * (size_t)nb * sizeof(double2)));
+        EF_CK(B.dEbar.ensure((size_t)nb * ((size_t)1 << B.r_loc) * sizeof(double2)));
+        EF_CK(B.dTbar.ensure(ny * std::max<size_t>(1, (size_t)B.L * B.n * B.n) * sizeof(double2)));
+        EF_CK(B.dSbar.ensure(ny * ne * sizeof(double2)));
+        EF_CK(B.dSumT.ensure(std::max<size_t>(1, (size_t)B.L * B.n * B.n) * sizeof(double2)));
+        EF_CK(B.dSumS.ensure(ne * sizeof(double2)));
+        EF_CK(B.dSumE.ensure(((size_t)1 << B.r_loc) * sizeof(double2)));
+        ef::ExactBlockDev& d = g.blk[b];
+        exact_block_geometry(c, b, nb, d);
+        d.S0C = B.dS0C.as<double2>();
+        d.T = B.dT.as<double2>();
+        d.F = B.dF.as<uint32_t>();
+        d.M64 = B.dM64.as<double2>();
+        d.M32 = nullptr;
+        d.D = B.dD.as<ef::d4>();
+        cm.mask[b][0] = B.mask[0];
+        cm.mask[b][1] = B.mask[1];
+        cm.eta[b] = B.eta;
+        cm.r[b] = B.r;
+        cm.r_loc[b] = B.r_loc;
+        cm.D[b] = d.D;
+        cm.Omega[b] = B.dOmega.as<double2>();
+        cm.s[b] = B.dSh.as<uint32_t>();
+        cm.perm[b] = B.dPerm.as<uint32_t>();
+        cm.goff[b] = B.dGoff.as<uint32_t>();
+        g.cot[b] = B.dCot.as<double2>();
+        g.ebar[b] = B.dEbar.as<double2>();
+        g.tbar[b] = B.dTbar.as<double2>();
+        g.sbar[b] = B.dSbar.as<double2>();
+    }
+    EF_CK(c->dPbar.ensure((size_t)nb * ((size_t)1 << ksh) * sizeof(double2)));
+    EF_CK(c->dSumP.ensure(((size_t)1 << ksh) * sizeof(double2)));
+    g.pbar = c->dPbar.as<double2>();
+    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_build_branches(g.blk[b], false, s, st));
+    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_exact_lu_f64(g.blk[b], d_bits, nb, nullptr, nullptr, nb, s, st));
+    if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
+    EF_CK(ef::launch_grad(g, d_bits, nb, d_grad_p, d_out_p, s, st));
+    if (c->timed) EF_CK(cudaEventRecord(c->ev1, s));
+    c->stats.dominant_kernel_launches = 1 + c->nblocks;
+    std::vector<std::vector<cd>> tbar(c->nblocks), sbar(c->nblocks), ebar(c->nblocks);
+    std::vector<cd> pbar;
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        const int64_t ny = (int64_t)1 << B.r;
+        const int64_t wT = (int64_t)B.L * B.n * B.n, wS = (int64_t)B.n * B.eta, wE = (int64_t)1 << B.r_loc;
+        EF_CK(ef::launch_sum_rows(B.dTbar.as<double2>(), ny, wT, wT, B.dSumT.as<double2>(), s, st));
+        EF_CK(ef::launch_sum_rows(B.dSbar.as<double2>(), ny, wS, wS, B.dSumS.as<double2>(), s, st));
+        EF_CK(ef::launch_sum_rows(B.dEbar.as<double2>(), nb, wE, wE, B.dSumE.as<double2>(), s, st));
+        tbar[b].resize(wT);
+        sbar[b].resize(wS);
+        ebar[b].resize(wE);
+        if (wT) EF_CK(cudaMemcpyAsync(tbar[b].data(), B.dSumT.p, wT * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        EF_CK(cudaMemcpyAsync(sbar[b].data(), B.dSumS.p, wS * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        EF_CK(cudaMemcpyAsync(ebar[b].data(), B.dSumE.p, wE * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    }
+    if (c->nblocks == 2) {
+        const int64_t wP = (int64_t)1 << ksh;
+        EF_CK(ef::launch_sum_rows(c->dPbar.as<double2>(), nb, wP, wP, c->dSumP.as<double2>(), s, st));
+        pbar.resize(wP);
+        EF_CK(cudaMemcpyAsync(pbar.data(), c->dSumP.p, wP * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    }
+    EF_CK(cudaStreamSynchronize(s));
+    c->stats.kernel_launches = st.launches;
+    c->stats.executed_minor_lus = 2 * st.executed_lus;
+    grad_finish(c, tbar, sbar, ebar, pbar, grad);
+    return EF_OK;
+}
+
 int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uint64_t seed, uint64_t base,
                double* d_out, double* d_se, cudaStream_t s) {
     if (!c->approx_ok) return fail(EF_EUNSUPPORTED, c->approx_why);
@@ -1083,16 +1342,46 @@ int ef_prob_approx(ef_circuit* c, const uint64_t* bits, int64_t nb, int64_t n_tr
 
 int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_grad_p, double* d_out_p,
                      double* d_grad_angles, void* stream) {
-    (void)d_bits; (void)nb; (void)d_grad_p; (void)d_out_p; (void)d_grad_angles; (void)stream;
     if (!c) return fail(EF_EINVAL, "NULL circuit");
-    return fail(EF_EUNSUPPORTED, "ef_prob_grad: adjoint path not built yet");
+    if (nb < 0 || (nb > 0 && (!d_bits || !d_grad_p)) || !d_grad_angles)
+        return fail(EF_EINVAL, "bad bitstring/gradient arguments");
+    if (nb > 2147483647ll) return fail(EF_EUNSUPPORTED, "more than 2^31-1 bitstrings per call");
+    std::vector<double> grad;
+    const cudaStream_t s = (cudaStream_t)stream;
+    int rc = grad_dev(c, d_bits, nb, d_grad_p, d_out_p, grad, s);
+    if (rc) return rc;
+    if (!grad.empty()) {
+        EF_CK(cudaMemcpyAsync(d_grad_angles, grad.data(), grad.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        EF_CK(cudaStreamSynchronize(s));
+    }
+    return EF_OK;
 }
 
 int ef_prob_grad(ef_circuit* c, const uint64_t* bits, int64_t nb, const double* grad_p, double* out_p,
                  double* grad_angles) {
-    (void)bits; (void)nb; (void)grad_p; (void)out_p; (void)grad_angles;
     if (!c) return fail(EF_EINVAL, "NULL circuit");
-    return fail(EF_EUNSUPPORTED, "ef_prob_grad: adjoint path not built yet");
+    if (nb < 0 || (nb > 0 && (!bits || !grad_p)) || !grad_angles) return fail(EF_EINVAL, "bad arguments");
+    int rc = check_bits_host(c, bits, nb);
+    if (rc) return rc;
+    if (!c->own_stream) EF_CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    const cudaStream_t s = c->own_stream;
+    if (nb > 0) {
+        EF_CK(c->dBits.ensure((size_t)nb * 2 * sizeof(uint64_t)));
+        EF_CK(c->dGradP.ensure((size_t)nb * sizeof(double)));
+        EF_CK(c->dOut.ensure((size_t)nb * sizeof(double)));
+        EF_CK(cudaMemcpyAsync(c->dBits.p, bits, (size_t)nb * 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+        EF_CK(cudaMemcpyAsync(c->dGradP.p, grad_p, (size_t)nb * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    std::vector<double> grad;
+    rc = grad_dev(c, c->dBits.as<uint64_t>(), nb, c->dGradP.as<double>(), nb > 0 ? c->dOut.as<double>() : nullptr,
+                  grad, s);
+    if (rc) return rc;
+    if (out_p && nb > 0) {
+        EF_CK(cudaMemcpyAsync(out_p, c->dOut.p, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EF_CK(cudaStreamSynchronize(s));
+    }
+    std::copy(grad.begin(), grad.end(), grad_angles);
+    return EF_OK;
 }
 
 int ef_circuit_get_stats(ef_circuit* c, ef_stats* st) {

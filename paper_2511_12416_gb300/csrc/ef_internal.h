@@ -99,6 +99,18 @@ struct ApproxDev {
     ApproxBlockDev blk[kMaxBlocks];
 };
 
+// ---------------------------------------------------------------- adjoint
+
+struct GradDev {
+    ExactCombineDev cm;             // forward tables (D holds FP64 determinants)
+    ExactBlockDev blk[kMaxBlocks];  // FP64 branch matrices, layer tables
+    double2* cot[kMaxBlocks];       // [2^r][nb]: gamma_b d amp_b / d det_B(b, z)
+    double2* ebar[kMaxBlocks];      // [nb][2^r_loc]: gamma_b d amp_b / d Omega_B(z)
+    double2* pbar;                  // [nb][2^k_sh]: gamma_b d amp_b / d w_sh(x_sh)
+    double2* tbar[kMaxBlocks];      // [2^r][L][n][n]: per-pattern d L / d T_l
+    double2* sbar[kMaxBlocks];      // [2^r][n][eta]: per-pattern d L / d S_0[:, C]
+};
+
 // ---------------------------------------------------------------- launchers
 
 struct LaunchStats {
@@ -121,6 +133,11 @@ cudaError_t launch_exact_lu_rows(const ExactBlockDev& b, const uint64_t* bits, i
 cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits, int64_t nb, int64_t stride,
                                  const int* list, const int* list_count, double* out, double* err,
                                  int* append_list, int* append_count, cudaStream_t s, LaunchStats& st);
+cudaError_t launch_grad(const GradDev& g, const uint64_t* bits, int64_t nb, const double* grad_p,
+                        double* out_p, cudaStream_t s, LaunchStats& st);
+size_t grad_minors_smem(int n, int eta, int L);
+cudaError_t launch_sum_rows(const double2* in, int64_t count, int64_t stride, int64_t width, double2* out,
+                            cudaStream_t s, LaunchStats& st);
 cudaError_t launch_approx(const ApproxDev& a, const uint64_t* bits, int64_t nb, bool fp64,
                           cudaStream_t s, LaunchStats& st);
 cudaError_t launch_approx_finalize(const ApproxDev& a, int64_t nb, double* out, double* stderr_out,

@@ -1,0 +1,131 @@
+"""GPU adjoint (ef_prob_grad, FP64) against the oracle's forward-mode
+derivative and against central finite differences.
+
+Criteria: against the oracle, |g - g_ref| <= 1e-9 * max(1, |g_ref|_inf)
+(both FP64, different arithmetic orders); against central differences of
+the GPU FP64 forward pass (h = 1e-6),
+|g . v - FD| <= 1e-6 * max(1, |g|_inf |v|_1)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_grad(lib, c, bits, g):
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_FP64)
+    try:
+        return lib.ef_prob_grad(h, bits, g)
+    finally:
+        lib.ef_circuit_destroy(h)
+
+
+SMALL = [
+    ("config1", lambda: W.config1()),
+    ("random-n8-eta3-k5", lambda: (W.random_fig4_circuit(8, 3, 5, 2, seed=21), W.sector_bitstrings_all(8, 3))),
+    ("random-n10-eta4-k6-sparse", lambda: (W.random_fig4_circuit(10, 4, 6, 1, seed=23, angle_std=2.0),
+                                           W.sector_bitstrings_all(10, 4)[:80])),
+    ("lucj-8q-2layer", lambda: (W.lucj_circuit(4, 2, 2, 2, n_onsite=2, n_same=1, angle_sampler=W.normal_var(0.5),
+                                               seed=13), W.spin_sector_bitstrings_all(4, 2, 2))),
+    ("lucj-10q-1layer", lambda: (W.lucj_circuit(5, 2, 3, 1, n_onsite=3, n_same=2, angle_sampler=W.normal_var(0.3),
+                                                seed=14), W.spin_sector_bitstrings_all(5, 2, 3))),
+]
+
+
+@pytest.mark.parametrize("name,maker", SMALL, ids=[s[0] for s in SMALL])
+def test_grad_matches_oracle_all_angles(lib, name, maker):
+    c, bits = maker()
+    rng = np.random.default_rng(7)
+    g = rng.uniform(-1, 1, len(bits))
+    p, grad = gpu_grad(lib, c, bits, g)
+    ref = O.prob_gradient(c, bits, g)
+    assert np.max(np.abs(grad - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(p - O.exact_probabilities(c, bits))) < 1e-12
+
+
+def test_grad_edge_cases(lib):
+    c, bits = W.config1()
+    na = len(O.get_angles(c.gates))
+    p, grad = gpu_grad(lib, c, np.zeros((0, 2), dtype=np.uint64), np.zeros(0))
+    assert len(p) == 0 and np.all(grad == 0) and len(grad) == na
+    # wrong-weight bitstrings contribute nothing
+    bad = np.array([W.modes_to_bits([0, 1, 2])], dtype=np.uint64)
+    p, grad = gpu_grad(lib, c, bad, np.ones(1))
+    assert p[0] == 0 and np.all(grad == 0)
+
+
+def _log_weights(p, w):
+    return w / p
+
+
+def test_grad_config5_subset_against_oracle(lib):
+    """Config 5's circuit (2x20 modes, 6a+6b, 2 layers, k=12) on 12 bitstrings:
+    random directions and sampled components against the oracle."""
+    c, bits, w = W.config5()
+    sub = bits[:12]
+    p_ref = O.exact_probabilities(c, sub)
+    g = w[:12] / p_ref
+    p, grad = gpu_grad(lib, c, sub, g)
+    assert np.max(np.abs(p - p_ref) / p_ref) < 1e-10
+    rng = np.random.default_rng(3)
+    na = len(grad)
+    scale = max(1.0, np.max(np.abs(grad)))
+    for _ in range(2):
+        v = rng.normal(size=na)
+        dref = O.prob_directional_derivative(c, sub, g, v)
+        assert abs(np.dot(grad, v) - dref) <= 1e-9 * scale * np.sum(np.abs(v))
+    idx = rng.choice(na, 6, replace=False).tolist() + [na - 1]
+    ref = O.prob_gradient(c, sub, g, angle_indices=idx)
+    assert np.max(np.abs(grad[idx] - ref)) <= 1e-9 * scale
+
+
+def test_grad_config5_full_against_finite_differences(lib):
+    """All 4096 bitstrings, L = sum_b w_b log p_b, adjoint against central
+    differences (h = 1e-6) of the GPU FP64 forward pass."""
+    c, bits, w = W.config5()
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_FP64)
+    try:
+        p = lib.ef_prob_exact(h, bits)
+        ang = lib.ef_circuit_get_angles(h)
+        _, grad = lib.ef_prob_grad(h, bits, w / p)
+
+        def L(a):
+            lib.ef_circuit_set_angles(h, a)
+            return float(np.dot(w, np.log(lib.ef_prob_exact(h, bits))))
+
+        rng = np.random.default_rng(11)
+        hstep = 1e-6
+        scale = max(1.0, np.max(np.abs(grad)))
+        dirs = [rng.normal(size=len(ang)) for _ in range(2)]
+        for j in rng.choice(len(ang), 4, replace=False):
+            e = np.zeros(len(ang))
+            e[j] = 1.0
+            dirs.append(e)
+        for v in dirs:
+            fd = (L(ang + hstep * v) - L(ang - hstep * v)) / (2 * hstep)
+            assert abs(np.dot(grad, v) - fd) <= 1e-6 * scale * np.sum(np.abs(v)), (np.dot(grad, v), fd)
+    finally:
+        lib.ef_circuit_destroy(h)
+
+
+def test_autograd_function(lib):
+    torch = pytest.importorskip("torch")
+    from paper_2511_12416_gb300.autograd import BornProbabilities
+    c, bits = W.lucj_circuit(4, 2, 2, 2, n_onsite=2, n_same=1, angle_sampler=W.normal_var(0.5), seed=13), \
+        W.spin_sector_bitstrings_all(4, 2, 2)
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_FP64)
+    try:
+        ang = torch.tensor(O.get_angles(c.gates), dtype=torch.float64, requires_grad=True)
+        dbits = torch.from_numpy(bits.view(np.int64)).cuda()
+        wts = torch.linspace(0.1, 1.0, len(bits), dtype=torch.float64, device="cuda")
+        p = BornProbabilities.apply(ang, h, dbits)
+        loss = (wts * torch.log(p)).sum()
+        loss.backward()
+        g_ref = O.prob_gradient(c, bits, (wts / p).detach().cpu().numpy())
+        assert np.max(np.abs(ang.grad.numpy() - g_ref)) <= 1e-9 * max(1.0, np.max(np.abs(g_ref)))
+    finally:
+        lib.ef_circuit_destroy(h)
