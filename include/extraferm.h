@@ -203,6 +203,35 @@ int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const do
 int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out,
                               double* d_err_out, void* stream);
 
+/* ---- Multi-circuit batch (no counterpart in the paper; Section IV-A runs
+ * one circuit at a time). A batch evaluates many circuits of uneven modes,
+ * particles and controlled-phase gates in one CUDA graph: Exact circuits
+ * with FP32 minors share persistent work-queue LU kernels (one per particle
+ * count) whose chunk sizes are chosen on first use by timing; Raw Estimate
+ * circuits and the per-circuit sums run on forked streams. The batch does
+ * not own the circuits; destroy it before them. */
+typedef struct ef_batch ef_batch;
+
+/* Create a batch over circuits cs[0..nc). */
+int ef_batch_create(ef_circuit* const* cs, int32_t nc, ef_batch** out);
+
+/* Release a batch (waits for its work). NULL is allowed. */
+int ef_batch_destroy(ef_batch* b);
+
+/* Probabilities of every circuit of the batch. All arrays are host arrays
+ * of length nc: d_bits[i] (device, nb[i] x 2 uint64) and d_out[i] (device,
+ * nb[i] doubles) for circuit i; n_traj[i] = 0 selects the Exact algorithm
+ * (in the circuit's precision mode), n_traj[i] > 0 the Raw Estimate with
+ * that many trajectories (seed `seed`, global bitstring indices 0..nb[i]-1).
+ * The first call with a given set of arguments plans, runs and captures the
+ * work (synchronous); later calls with the same arguments replay the graph on
+ * `stream` (asynchronous). Changing a circuit's angles re-plans. */
+int ef_batch_prob_dev(ef_batch* b, const uint64_t* const* d_bits, const int64_t* nb, double* const* d_out,
+                      const int64_t* n_traj, uint64_t seed, void* stream);
+
+/* Kernel launches of one batch execution and the logical branch count. */
+int ef_batch_get_stats(ef_batch* b, ef_stats* st);
+
 /* Counters and timings of the circuit's last probability call (waits for it). */
 int ef_circuit_get_stats(ef_circuit* c, ef_stats* st);
 

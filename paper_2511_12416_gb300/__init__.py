@@ -70,6 +70,11 @@ SIGNATURES = {
     "ef_prob_grad_dev": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "ef_circuit_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(EfStats)]),
     "ef_prob_exact_noalloc_dev": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "ef_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P)]),
+    "ef_batch_destroy": (ctypes.c_int, [_P]),
+    "ef_batch_prob_dev": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P),
+                                         ctypes.POINTER(_I64), _U64, _P]),
+    "ef_batch_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(EfStats)]),
 }
 
 _lib = None
@@ -232,6 +237,33 @@ def ef_prob_grad_dev(c, d_bits: int, nb: int, d_grad_p: int, d_out_p: int, d_gra
 def ef_circuit_get_stats(c) -> dict:
     st = EfStats()
     _check(load().ef_circuit_get_stats(c, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def ef_batch_create(circuits):
+    """Batch over circuit handles (the batch does not own them)."""
+    arr = (_P * len(circuits))(*[c.value if isinstance(c, _P) else c for c in circuits])
+    h = _P()
+    _check(load().ef_batch_create(arr, len(circuits), ctypes.byref(h)))
+    return h
+
+
+def ef_batch_destroy(b):
+    if b:
+        _check(load().ef_batch_destroy(b))
+
+
+def ef_batch_prob_dev(b, d_bits, nb, d_out, n_traj, seed: int = 0, stream: int = 0):
+    """d_bits, d_out: sequences of device pointers; nb, n_traj: sequences of
+    ints (n_traj 0 = Exact, > 0 = Raw Estimate with that many trajectories)."""
+    n = len(nb)
+    _check(load().ef_batch_prob_dev(b, (_P * n)(*d_bits), (_I64 * n)(*nb), (_P * n)(*d_out), (_I64 * n)(*n_traj),
+                                    int(seed), stream or None))
+
+
+def ef_batch_get_stats(b) -> dict:
+    st = EfStats()
+    _check(load().ef_batch_get_stats(b, ctypes.byref(st)))
     return st.as_dict()
 
 

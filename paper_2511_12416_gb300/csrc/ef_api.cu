@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <map>
 #include <cstring>
 #include <new>
 #include <string>
@@ -528,7 +529,7 @@ int prepare(ef_circuit* c) {
         }
         if (B.eta > ef::kMaxApproxEta) {
             c->approx_ok = false;
-            c->approx_why = "Raw Estimate: more than 8 particles in one mode block";
+            c->approx_why = "Raw Estimate: more than 13 particles in one mode block";
         }
         if (L > ef::kMaxApproxLayers || nb_ > 64 || (L > 0 && (L - 1) * nb_ > ef::kMaxApproxStored)) {
             c->approx_ok = false;
@@ -714,21 +715,7 @@ void exact_block_geometry(const ef_circuit* c, int b, int64_t cap, ef::ExactBloc
     d.mask1 = B.mask[1];
 }
 
-int run_exact(ef_circuit* c, const ExactBuffers& eb, const uint64_t* d_bits, int64_t nb, double* d_out,
-              double* d_err, cudaStream_t s, ef::LaunchStats& st) {
-    const int prec = c->opt.precision;
-    const bool fp64_only = prec == EF_PREC_FP64;
-    const bool autofix = prec == EF_PREC_AUTO;
-    double flops = 0.0;
-    int64_t sub_total = 0;
-    for (int b = 0; b < c->nblocks; ++b) {
-        flops += (double)nb * std::ldexp(1.0, c->blk[b].r) * lu_flops(c->blk[b].eta);
-        sub_total += (int64_t)1 << c->blk[b].r;
-    }
-    c->last_sub_total = sub_total;
-    c->stats.dominant_kernel_flops = flops;
-    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_build_branches(eb.blk[b], !fp64_only, s, st));
-
+ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
     ef::ExactCombineDev cm{};
     cm.nblocks = c->nblocks;
     cm.k_sh = c->nblocks == 2 ? (int)c->shared_gates.size() : 0;
@@ -751,15 +738,81 @@ int run_exact(ef_circuit* c, const ExactBuffers& eb, const uint64_t* d_bits, int
     cm.WS32 = eb.WS32;
     cm.tol = c->opt.tol;
     cm.p_floor = c->p_floor;
-    // FP32 error model: per minor |d det|^2 ~ (K u32)^2 (|det|^2 er2 + zabs2),
-    // independent between distinct minors and propagated to the amplitude
-    // through each minor's coefficient. Observed errors behave like Gaussians
-    // whose standard deviation is about a third of the K = 1 estimate, so
-    // K = 4 bounds them at about 5 standard deviations (the largest ratio seen
-    // in 16,000 significant results was 0.76 at K = 4);
-    // ef_options.tile_override[1] > 0 sets K in tenths.
+    return cm;
+}
+
+// FP32 error model: per minor |d det|^2 ~ (K u32)^2 (|det|^2 er2 + zabs2),
+// independent between distinct minors and propagated to the amplitude
+// through each minor's coefficient. Observed errors behave like Gaussians
+// whose standard deviation is about a third of the K = 1 estimate, so K = 4
+// bounds them at about 5 standard deviations (the largest ratio seen in
+// 16,000 significant results was 0.76 at K = 4); ef_options.tile_override[1]
+// > 0 sets K in tenths.
+double fp32_err_coef(const ef_circuit* c) {
+    if (c->opt.precision == EF_PREC_FP64) return 0.0;
     const double K = c->opt.tile_override[1] > 0 ? 0.1 * c->opt.tile_override[1] : 4.0;
-    const double err_coef = fp64_only ? 0.0 : K * std::ldexp(1.0, -24);
+    return K * std::ldexp(1.0, -24);
+}
+
+void exact_account(ef_circuit* c, int64_t nb) {
+    double flops = 0.0;
+    int64_t sub_total = 0;
+    for (int b = 0; b < c->nblocks; ++b) {
+        flops += (double)nb * std::ldexp(1.0, c->blk[b].r) * lu_flops(c->blk[b].eta);
+        sub_total += (int64_t)1 << c->blk[b].r;
+    }
+    c->last_sub_total = sub_total;
+    c->stats.dominant_kernel_flops = flops;
+}
+
+int exact_enqueue_build(ef_circuit* c, const ExactBuffers& eb, cudaStream_t s, ef::LaunchStats& st) {
+    const bool fp64_only = c->opt.precision == EF_PREC_FP64;
+    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_build_branches(eb.blk[b], !fp64_only, s, st));
+    return EF_OK;
+}
+
+int exact_enqueue_lu(ef_circuit* c, const ExactBuffers& eb, const uint64_t* bits, int64_t nbb, cudaStream_t s,
+                     ef::LaunchStats& st) {
+    const bool fp64_only = c->opt.precision == EF_PREC_FP64;
+    for (int b = 0; b < c->nblocks; ++b) {
+        const ef::ExactBlockDev& d = eb.blk[b];
+        if (fp64_only) {
+            EF_CK(ef::launch_exact_lu_f64(d, bits, nbb, nullptr, nullptr, nbb, s, st));
+        } else if (d.eta <= ef::kMaxEtaThread) {
+            EF_CK(ef::launch_exact_lu_f32(d, bits, nbb, s, st));
+        } else {
+            EF_CK(ef::launch_exact_lu_rows(d, bits, nbb, nullptr, nullptr, nbb, false, s, st));
+        }
+    }
+    return EF_OK;
+}
+
+// combine, and under EF_PREC_AUTO the FP64 recompute of flagged results
+int exact_enqueue_combine(ef_circuit* c, const ExactBuffers& eb, ef::ExactCombineDev cm, const uint64_t* bits,
+                          int64_t nbb, double* out, double* err, cudaStream_t s, ef::LaunchStats& st) {
+    const bool autofix = c->opt.precision == EF_PREC_AUTO;
+    if (autofix) EF_CK(cudaMemsetAsync(eb.count, 0, sizeof(int), s));
+    cm.err_coef = fp32_err_coef(c);
+    cm.recomputed_total = nullptr;
+    EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, nullptr, nullptr, out, err, autofix ? eb.list : nullptr,
+                                   autofix ? eb.count : nullptr, s, st));
+    if (autofix) {
+        for (int b = 0; b < c->nblocks; ++b)
+            EF_CK(ef::launch_exact_lu_f64(eb.blk[b], bits, nbb, eb.list, eb.count, nbb, s, st));
+        cm.err_coef = 0.0;
+        cm.recomputed_total = eb.recomp;
+        EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, eb.list, eb.count, out, err, nullptr, nullptr, s, st));
+    }
+    return EF_OK;
+}
+
+int run_exact(ef_circuit* c, const ExactBuffers& eb, const uint64_t* d_bits, int64_t nb, double* d_out,
+              double* d_err, cudaStream_t s, ef::LaunchStats& st) {
+    const bool autofix = c->opt.precision == EF_PREC_AUTO;
+    exact_account(c, nb);
+    int rc = exact_enqueue_build(c, eb, s, st);
+    if (rc) return rc;
+    const ef::ExactCombineDev cm = make_combine(c, eb);
     if (autofix) {
         EF_CK(cudaMemsetAsync(eb.recomp, 0, sizeof(int), s));
         c->last_recomp = eb.recomp;
@@ -769,34 +822,14 @@ int run_exact(ef_circuit* c, const ExactBuffers& eb, const uint64_t* d_bits, int
     for (int64_t off = 0; off < nb; off += eb.cap) {
         const int64_t nbb = std::min(eb.cap, nb - off);
         const uint64_t* bits = d_bits + 2 * off;
-        double* out = d_out + off;
-        double* err = d_err ? d_err + off : nullptr;
         if (c->timed && off == 0) EF_CK(cudaEventRecord(c->ev0, s));
         const int64_t before = st.launches;
-        for (int b = 0; b < c->nblocks; ++b) {
-            const ef::ExactBlockDev& d = eb.blk[b];
-            if (fp64_only) {
-                EF_CK(ef::launch_exact_lu_f64(d, bits, nbb, nullptr, nullptr, nbb, s, st));
-            } else if (d.eta <= ef::kMaxEtaThread) {
-                EF_CK(ef::launch_exact_lu_f32(d, bits, nbb, s, st));
-            } else {
-                EF_CK(ef::launch_exact_lu_rows(d, bits, nbb, nullptr, nullptr, nbb, false, s, st));
-            }
-        }
+        rc = exact_enqueue_lu(c, eb, bits, nbb, s, st);
+        if (rc) return rc;
         lu_launches += st.launches - before;
         if (c->timed && off + nbb >= nb) EF_CK(cudaEventRecord(c->ev1, s));
-        if (autofix) EF_CK(cudaMemsetAsync(eb.count, 0, sizeof(int), s));
-        cm.err_coef = err_coef;
-        cm.recomputed_total = nullptr;
-        EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, nullptr, nullptr, out, err, autofix ? eb.list : nullptr,
-                                       autofix ? eb.count : nullptr, s, st));
-        if (autofix) {
-            for (int b = 0; b < c->nblocks; ++b)
-                EF_CK(ef::launch_exact_lu_f64(eb.blk[b], bits, nbb, eb.list, eb.count, nbb, s, st));
-            cm.err_coef = 0.0;
-            cm.recomputed_total = eb.recomp;
-            EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, eb.list, eb.count, out, err, nullptr, nullptr, s, st));
-        }
+        rc = exact_enqueue_combine(c, eb, cm, bits, nbb, d_out + off, d_err ? d_err + off : nullptr, s, st);
+        if (rc) return rc;
     }
     c->stats.dominant_kernel_launches = lu_launches;
     c->stats.kernel_launches = st.launches;
@@ -804,24 +837,20 @@ int run_exact(ef_circuit* c, const ExactBuffers& eb, const uint64_t* d_bits, int
     return EF_OK;
 }
 
-int exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out, double* d_err, cudaStream_t s) {
-    if (!c->exact_ok) return fail(EF_EUNSUPPORTED, c->exact_why);
-    int rc = begin_call(c, s, 1);
-    if (rc) return rc;
+// Workspace and device pointers of an Exact call with batches of `cap` bitstrings.
+int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
     const bool fp64_only = c->opt.precision == EF_PREC_FP64;
-    c->stats.logical_branch_dets = nb * (int64_t)std::ldexp(1.0, (int)c->cps.size());
-    if (nb == 0) return EF_OK;
-    ExactBuffers eb{};
-    eb.cap = exact_batch(c, nb, (size_t)2 << 30);
+    eb = ExactBuffers{};
+    eb.cap = cap;
     for (int b = 0; b < c->nblocks; ++b) {
         HostBlock& B = c->blk[b];
         const size_t ny = (size_t)1 << B.r;
         const size_t ne = (size_t)B.n * B.eta;
         EF_CK(B.dM64.ensure(ny * ne * sizeof(double2)));
         if (!fp64_only) EF_CK(B.dM32.ensure(ny * ne * sizeof(float2)));
-        EF_CK(B.dD.ensure(ny * (size_t)eb.cap * sizeof(ef::d4)));
+        EF_CK(B.dD.ensure(ny * (size_t)cap * sizeof(ef::d4)));
         ef::ExactBlockDev& d = eb.blk[b];
-        exact_block_geometry(c, b, eb.cap, d);
+        exact_block_geometry(c, b, cap, d);
         d.S0C = B.dS0C.as<double2>();
         d.T = B.dT.as<double2>();
         d.F = B.dF.as<uint32_t>();
@@ -836,12 +865,24 @@ int exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out, 
     }
     eb.WS = c->dWS.as<double2>();
     eb.WS32 = c->dWS32.as<float2>();
-    EF_CK(c->dList.ensure((size_t)eb.cap * sizeof(int)));
+    EF_CK(c->dList.ensure((size_t)cap * sizeof(int)));
     EF_CK(c->dListCount.ensure(sizeof(int)));
     EF_CK(c->dRecomp.ensure(sizeof(int)));
     eb.list = c->dList.as<int>();
     eb.count = c->dListCount.as<int>();
     eb.recomp = c->dRecomp.as<int>();
+    return EF_OK;
+}
+
+int exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out, double* d_err, cudaStream_t s) {
+    if (!c->exact_ok) return fail(EF_EUNSUPPORTED, c->exact_why);
+    int rc = begin_call(c, s, 1);
+    if (rc) return rc;
+    c->stats.logical_branch_dets = nb * (int64_t)std::ldexp(1.0, (int)c->cps.size());
+    if (nb == 0) return EF_OK;
+    ExactBuffers eb;
+    rc = exact_buffers(c, exact_batch(c, nb, (size_t)2 << 30), eb);
+    if (rc) return rc;
     ef::LaunchStats st;
     return run_exact(c, eb, d_bits, nb, d_out, d_err, s, st);
 }
@@ -1091,17 +1132,17 @@ int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_
     return EF_OK;
 }
 
-int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uint64_t seed, uint64_t base,
-               double* d_out, double* d_se, cudaStream_t s) {
+// Buffers and launch parameters of a Raw Estimate call (no stream work).
+int approx_setup(ef_circuit* c, int64_t nb, int64_t t, uint64_t seed, uint64_t base, ef::ApproxDev& a) {
     if (!c->approx_ok) return fail(EF_EUNSUPPORTED, c->approx_why);
+    if (c->opt.precision == EF_PREC_FP64)
+        for (int b = 0; b < c->nblocks; ++b)
+            if (c->blk[b].eta > ef::kMaxApproxEta64)
+                return fail(EF_EUNSUPPORTED, "Raw Estimate with FP64 minors: at most 8 particles per mode block");
     if (t <= 0 || t > (int64_t)4294967296ll) return fail(EF_EINVAL, "n_traj must be in 1..2^32");
-    int rc = begin_call(c, s, 2);
-    if (rc) return rc;
+    if (nb > 2147483647ll) return fail(EF_EUNSUPPORTED, "Raw Estimate: more than 2^31-1 bitstrings per call");
     const bool fp64 = c->opt.precision == EF_PREC_FP64;
-    ef::LaunchStats st;
-    c->stats.logical_branch_dets = nb * t;
-    if (nb == 0) return EF_OK;
-    ef::ApproxDev a{};
+    a = ef::ApproxDev{};
     a.nblocks = c->nblocks;
     a.k = (int)c->cps.size();
     a.T = c->daT.as<uint32_t>();
@@ -1122,10 +1163,8 @@ int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uin
         a.traj_per_cta = (a.traj_per_cta + 127) / 128 * 128;
         a.n_chunks = (int)((t + a.traj_per_cta - 1) / a.traj_per_cta);
     }
-    if (nb > 2147483647ll) return fail(EF_EUNSUPPORTED, "Raw Estimate: more than 2^31-1 bitstrings per call");
-    EF_CK(c->daPart.ensure((size_t)nb * a.n_chunks * 8 * sizeof(double)));
+    EF_CK(c->daPart.ensure((size_t)std::max<int64_t>(nb, 1) * a.n_chunks * 8 * sizeof(double)));
     EF_CK(c->dCounters.ensure(4 * sizeof(unsigned long long)));
-    EF_CK(cudaMemsetAsync(c->dCounters.p, 0, 4 * sizeof(unsigned long long), s));
     a.part = c->daPart.as<double>();
     a.counters = c->dCounters.as<unsigned long long>();
     for (int b = 0; b < c->nblocks; ++b) {
@@ -1139,11 +1178,35 @@ int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uin
         a.blk[b].RC = fp64 ? B.dRC64.p : B.dRC32.p;
         a.blk[b].cols = B.dCols.as<int>();
     }
+    return EF_OK;
+}
+
+int approx_enqueue(ef_circuit* c, const ef::ApproxDev& a, const uint64_t* d_bits, int64_t nb, double* d_out,
+                   double* d_se, cudaStream_t s, ef::LaunchStats& st) {
+    const bool fp64 = c->opt.precision == EF_PREC_FP64;
+    EF_CK(cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned long long), s));
     if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
     EF_CK(ef::launch_approx(a, d_bits, nb, fp64, s, st));
     if (c->timed) EF_CK(cudaEventRecord(c->ev1, s));
-    c->stats.dominant_kernel_launches = 1;
     EF_CK(ef::launch_approx_finalize(a, nb, d_out, d_se, s, st));
+    return EF_OK;
+}
+
+int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uint64_t seed, uint64_t base,
+               double* d_out, double* d_se, cudaStream_t s) {
+    if (!c->approx_ok) return fail(EF_EUNSUPPORTED, c->approx_why);
+    if (t <= 0 || t > (int64_t)4294967296ll) return fail(EF_EINVAL, "n_traj must be in 1..2^32");
+    int rc = begin_call(c, s, 2);
+    if (rc) return rc;
+    c->stats.logical_branch_dets = nb * t;
+    if (nb == 0) return EF_OK;
+    ef::ApproxDev a;
+    rc = approx_setup(c, nb, t, seed, base, a);
+    if (rc) return rc;
+    ef::LaunchStats st;
+    rc = approx_enqueue(c, a, d_bits, nb, d_out, d_se, s, st);
+    if (rc) return rc;
+    c->stats.dominant_kernel_launches = 1;
     c->stats.kernel_launches = st.launches;
     return EF_OK;
 }
@@ -1578,4 +1641,365 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
     EF_CK(copy_in_c(eb.WS, c->WS.data(), c->WS.size(), s));
     EF_CK(copy_in(eb.WS32, c->WS32, s));
     return run_exact(c, eb, d_bits, nb, d_out, d_err_out, s, st);
+}
+
+// =================================================================== multi-circuit batch
+//
+// A batch runs many circuits of uneven size in one CUDA graph. Exact
+// circuits (FP32 minors) share persistent work-queue LU kernels, one per
+// particle count, whose CTAs pull (circuit block, bitstring tile, pattern
+// chunk) items from a device counter; the pattern-chunk size of every queue
+// is chosen on first use by timing the candidates on the batch's own data.
+// Raw Estimate circuits and the per-circuit combines run on forked streams.
+// The first call for a given set of arguments plans, runs the work directly
+// (its results are final) and captures the graph; later calls with the same
+// arguments replay it.
+
+struct ef_batch {
+    std::vector<ef_circuit*> cs;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> key;
+    struct Item {
+        int mode = 0;  // 1 exact via the work queues, 2 exact on its own launches, 3 Raw Estimate
+        ExactBuffers eb{};
+        ef::ApproxDev a{};
+        const uint64_t* bits = nullptr;
+        int64_t nb = 0;
+        double* out = nullptr;
+    };
+    std::vector<Item> items;
+    struct Class {
+        int eta = 0;
+        int first = 0, count = 0;  // entries [first, first + count)
+        int64_t n_items = 0;
+        size_t smem = 0;
+    };
+    std::vector<Class> classes;
+    std::vector<ef::QueueEntry> entries;
+    std::vector<std::pair<int, int>> entry_src;  // (item, block) of each entry
+    DBuf dEntries, dHeads;
+    std::map<int, int> tuned;  // eta -> pattern-chunk log2
+    int64_t launches = 0;
+    int64_t logical = 0;
+
+    ~ef_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (cudaStream_t s : side) cudaStreamDestroy(s);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (cap) cudaStreamDestroy(cap);
+        dEntries.release();
+        dHeads.release();
+    }
+};
+
+namespace {
+
+constexpr int kBatchSide = 4;
+
+// Fill the queue entries of class k with chunk size 2^cl (capped per entry).
+void batch_layout_class(ef_batch* bt, int k, int cl) {
+    ef_batch::Class& C = bt->classes[k];
+    int64_t begin = 0;
+    size_t smem = 0;
+    for (int e = C.first; e < C.first + C.count; ++e) {
+        ef::QueueEntry& E = bt->entries[e];
+        const HostBlock& B = bt->cs[bt->entry_src[e].first]->blk[bt->entry_src[e].second];
+        int c = std::min(cl, B.r);
+        while (c > 0 && ((size_t)1 << c) * B.n * (size_t)(B.eta | 1) * sizeof(float2) > 48 * 1024) --c;
+        E.blk.c_log2 = c;
+        E.blk.n_chunks = 1 << (B.r - c);
+        E.tiles = (E.nb + 127) / 128;
+        E.item_begin = begin;
+        begin += E.tiles * E.blk.n_chunks;
+        smem = std::max(smem, ((size_t)1 << c) * B.n * (size_t)(B.eta | 1) * sizeof(float2));
+    }
+    C.n_items = begin;
+    C.smem = smem;
+}
+
+int batch_upload_entries(ef_batch* bt) {
+    EF_CK(bt->dEntries.ensure(std::max<size_t>(1, bt->entries.size()) * sizeof(ef::QueueEntry)));
+    if (!bt->entries.empty())
+        EF_CK(cudaMemcpy(bt->dEntries.p, bt->entries.data(), bt->entries.size() * sizeof(ef::QueueEntry),
+                         cudaMemcpyHostToDevice));
+    return EF_OK;
+}
+
+int batch_launch_queue(ef_batch* bt, int k, cudaStream_t s, ef::LaunchStats& st) {
+    const ef_batch::Class& C = bt->classes[k];
+    unsigned long long* head = bt->dHeads.as<unsigned long long>() + k;
+    EF_CK(cudaMemsetAsync(head, 0, sizeof(unsigned long long), s));
+    const ef::QueueEntry* q = bt->dEntries.as<ef::QueueEntry>() + C.first;
+    EF_CK(ef::launch_queue_lu_f32(C.eta, q, C.count, C.n_items, head, C.smem, 0, s, st));
+    return EF_OK;
+}
+
+// Every launch of one batch execution (direct or under capture).
+int batch_enqueue(ef_batch* bt, cudaStream_t s, ef::LaunchStats& st) {
+    const int ns = (int)bt->side.size();
+    EF_CK(cudaEventRecord(bt->ev[0], s));
+    for (int k = 0; k < ns; ++k) EF_CK(cudaStreamWaitEvent(bt->side[k], bt->ev[0], 0));
+    int rr = 0;
+    for (size_t i = 0; i < bt->items.size(); ++i) {
+        ef_batch::Item& it = bt->items[i];
+        if (it.mode != 3 || it.nb == 0) continue;
+        int rc = approx_enqueue(bt->cs[i], it.a, it.bits, it.nb, it.out, nullptr, bt->side[rr++ % ns], st);
+        if (rc) return rc;
+    }
+    for (size_t i = 0; i < bt->items.size(); ++i) {
+        ef_batch::Item& it = bt->items[i];
+        if ((it.mode != 1 && it.mode != 2) || it.nb == 0) continue;
+        ef_circuit* c = bt->cs[i];
+        int rc = exact_enqueue_build(c, it.eb, s, st);
+        if (rc) return rc;
+        if (c->opt.precision == EF_PREC_AUTO) EF_CK(cudaMemsetAsync(it.eb.recomp, 0, sizeof(int), s));
+    }
+    for (size_t k = 0; k < bt->classes.size(); ++k) {
+        int rc = batch_launch_queue(bt, (int)k, s, st);
+        if (rc) return rc;
+    }
+    EF_CK(cudaEventRecord(bt->ev[1], s));
+    for (int k = 0; k < ns; ++k) EF_CK(cudaStreamWaitEvent(bt->side[k], bt->ev[1], 0));
+    for (size_t i = 0; i < bt->items.size(); ++i) {
+        ef_batch::Item& it = bt->items[i];
+        if ((it.mode != 1 && it.mode != 2) || it.nb == 0) continue;
+        ef_circuit* c = bt->cs[i];
+        cudaStream_t ss = bt->side[rr++ % ns];
+        const ef::ExactCombineDev cm = make_combine(c, it.eb);
+        if (it.mode == 1) {
+            int rc = exact_enqueue_combine(c, it.eb, cm, it.bits, it.nb, it.out, nullptr, ss, st);
+            if (rc) return rc;
+            continue;
+        }
+        // circuits outside the work queues: their own launches, slice by slice
+        for (int64_t off = 0; off < it.nb; off += it.eb.cap) {
+            const int64_t nbb = std::min(it.eb.cap, it.nb - off);
+            int rc = exact_enqueue_lu(c, it.eb, it.bits + 2 * off, nbb, ss, st);
+            if (rc) return rc;
+            rc = exact_enqueue_combine(c, it.eb, cm, it.bits + 2 * off, nbb, it.out + off, nullptr, ss, st);
+            if (rc) return rc;
+        }
+    }
+    for (int k = 0; k < ns; ++k) {
+        EF_CK(cudaEventRecord(bt->ev[2 + k], bt->side[k]));
+        EF_CK(cudaStreamWaitEvent(s, bt->ev[2 + k], 0));
+    }
+    return EF_OK;
+}
+
+// Time each candidate pattern-chunk size of class k on the batch's data.
+int batch_autotune(ef_batch* bt, int k, cudaStream_t s) {
+    const int eta = bt->classes[k].eta;
+    auto it = bt->tuned.find(eta);
+    if (it != bt->tuned.end()) {
+        batch_layout_class(bt, k, it->second);
+        return EF_OK;
+    }
+    cudaEvent_t e0, e1;
+    EF_CK(cudaEventCreate(&e0));
+    EF_CK(cudaEventCreate(&e1));
+    int best_c = 0;
+    float best_ms = 1e30f;
+    for (int cl = 1; cl <= 5; ++cl) {
+        batch_layout_class(bt, k, cl);
+        int rc = batch_upload_entries(bt);
+        if (rc) return rc;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            ef::LaunchStats st;
+            EF_CK(cudaEventRecord(e0, s));
+            rc = batch_launch_queue(bt, k, s, st);
+            if (rc) return rc;
+            EF_CK(cudaEventRecord(e1, s));
+            EF_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            EF_CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best_c = cl;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bt->tuned[eta] = best_c;
+    batch_layout_class(bt, k, best_c);
+    return EF_OK;
+}
+
+}  // namespace
+
+extern "C" int ef_batch_create(ef_circuit* const* cs, int32_t nc, ef_batch** out) {
+    if (!out) return fail(EF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nc <= 0 || !cs) return fail(EF_EINVAL, "a batch needs at least one circuit");
+    for (int i = 0; i < nc; ++i)
+        if (!cs[i]) return fail(EF_EINVAL, "NULL circuit in batch");
+    ef_batch* bt = new (std::nothrow) ef_batch();
+    if (!bt) return fail(EF_ENOMEM, "host allocation failed");
+    bt->cs.assign(cs, cs + nc);
+    cudaError_t e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
+    for (int k = 0; k < kBatchSide && e == cudaSuccess; ++k) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) bt->side.push_back(s);
+    }
+    for (int k = 0; k < 2 + kBatchSide && e == cudaSuccess; ++k) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) bt->ev.push_back(ev);
+    }
+    if (e == cudaSuccess) e = bt->dHeads.ensure(64 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        delete bt;
+        return fail(EF_ECUDA, std::string("ef_batch_create: ") + cudaGetErrorString(e));
+    }
+    *out = bt;
+    return EF_OK;
+}
+
+extern "C" int ef_batch_destroy(ef_batch* bt) {
+    if (!bt) return EF_OK;
+    if (bt->cap) cudaStreamSynchronize(bt->cap);
+    for (cudaStream_t s : bt->side) cudaStreamSynchronize(s);
+    delete bt;
+    return EF_OK;
+}
+
+extern "C" int ef_batch_prob_dev(ef_batch* bt, const uint64_t* const* d_bits, const int64_t* nb,
+                                 double* const* d_out, const int64_t* n_traj, uint64_t seed, void* stream) {
+    if (!bt) return fail(EF_EINVAL, "NULL batch");
+    if (!d_bits || !nb || !d_out || !n_traj) return fail(EF_EINVAL, "NULL argument array");
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int nc = (int)bt->cs.size();
+    std::vector<uint64_t> key = {seed};
+    bool dirty = false;
+    for (int i = 0; i < nc; ++i) {
+        if (nb[i] < 0 || (nb[i] > 0 && (!d_bits[i] || !d_out[i])) || n_traj[i] < 0)
+            return fail(EF_EINVAL, "bad arguments for circuit " + std::to_string(i));
+        key.insert(key.end(), {(uint64_t)(uintptr_t)d_bits[i], (uint64_t)nb[i], (uint64_t)(uintptr_t)d_out[i],
+                               (uint64_t)n_traj[i], (uint64_t)bt->cs[i]->opt.precision});
+        dirty = dirty || bt->cs[i]->dirty;
+    }
+    if (bt->exec && key == bt->key && !dirty) {
+        EF_CK(cudaGraphLaunch(bt->exec, s));
+        return EF_OK;
+    }
+    if (bt->exec) {
+        cudaGraphExecDestroy(bt->exec);
+        bt->exec = nullptr;
+    }
+    if (bt->graph) {
+        cudaGraphDestroy(bt->graph);
+        bt->graph = nullptr;
+    }
+    // plan: tables uploaded, buffers sized, modes chosen
+    bt->items.assign(nc, ef_batch::Item{});
+    bt->logical = 0;
+    for (int i = 0; i < nc; ++i) {
+        ef_circuit* c = bt->cs[i];
+        ef_batch::Item& it = bt->items[i];
+        it.bits = d_bits[i];
+        it.nb = nb[i];
+        it.out = d_out[i];
+        int rc;
+        if (n_traj[i] == 0) {
+            if (!c->exact_ok) return fail(EF_EUNSUPPORTED, "circuit " + std::to_string(i) + ": " + c->exact_why);
+            rc = begin_call(c, s, 1);
+            if (rc) return rc;
+            const int64_t cap = exact_batch(c, std::max<int64_t>(nb[i], 1), (size_t)2 << 30);
+            rc = exact_buffers(c, cap, it.eb);
+            if (rc) return rc;
+            bool q = cap >= nb[i] && c->opt.precision != EF_PREC_FP64;
+            for (int b = 0; b < c->nblocks; ++b) q = q && c->blk[b].eta <= ef::kMaxEtaThread;
+            it.mode = q ? 1 : 2;
+            bt->logical += nb[i] * (int64_t)std::ldexp(1.0, (int)c->cps.size());
+        } else {
+            rc = begin_call(c, s, 2);
+            if (rc) return rc;
+            rc = approx_setup(c, nb[i], n_traj[i], seed, 0, it.a);
+            if (rc) return rc;
+            it.mode = 3;
+            bt->logical += nb[i] * n_traj[i];
+        }
+    }
+    EF_CK(cudaStreamSynchronize(s));
+    // work-queue classes by particle count
+    bt->classes.clear();
+    bt->entries.clear();
+    bt->entry_src.clear();
+    std::map<int, std::vector<std::pair<int, int>>> by_eta;
+    for (int i = 0; i < nc; ++i)
+        if (bt->items[i].mode == 1 && bt->items[i].nb > 0)
+            for (int b = 0; b < bt->cs[i]->nblocks; ++b) by_eta[bt->cs[i]->blk[b].eta].push_back({i, b});
+    if ((int)by_eta.size() > 64) return fail(EF_EUNSUPPORTED, "more than 64 particle-count classes");
+    for (auto& kv : by_eta) {
+        ef_batch::Class C;
+        C.eta = kv.first;
+        C.first = (int)bt->entries.size();
+        // larger pieces first: fewer stragglers at the end of the queue
+        std::vector<std::pair<int, int>> src = kv.second;
+        std::stable_sort(src.begin(), src.end(), [&](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+            const double wx = (double)bt->items[x.first].nb * std::ldexp(1.0, bt->cs[x.first]->blk[x.second].r);
+            const double wy = (double)bt->items[y.first].nb * std::ldexp(1.0, bt->cs[y.first]->blk[y.second].r);
+            return wx > wy;
+        });
+        for (auto& pr : src) {
+            ef::QueueEntry E{};
+            E.blk = bt->items[pr.first].eb.blk[pr.second];
+            E.bits = bt->items[pr.first].bits;
+            E.nb = bt->items[pr.first].nb;
+            bt->entries.push_back(E);
+            bt->entry_src.push_back(pr);
+        }
+        C.count = (int)bt->entries.size() - C.first;
+        bt->classes.push_back(C);
+    }
+    // branch matrices first (the autotuner times real work), then tune, then run
+    ef::LaunchStats st0;
+    for (int i = 0; i < nc; ++i)
+        if (bt->items[i].mode == 1 && bt->items[i].nb > 0) {
+            int rc = exact_enqueue_build(bt->cs[i], bt->items[i].eb, s, st0);
+            if (rc) return rc;
+        }
+    for (size_t k = 0; k < bt->classes.size(); ++k) {
+        int rc = batch_autotune(bt, (int)k, s);
+        if (rc) return rc;
+    }
+    int rc = batch_upload_entries(bt);
+    if (rc) return rc;
+    ef::LaunchStats st;
+    rc = batch_enqueue(bt, s, st);
+    if (rc) return rc;
+    bt->launches = st.launches;
+    // capture the same work for later calls
+    EF_CK(cudaStreamSynchronize(s));
+    EF_CK(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeRelaxed));
+    ef::LaunchStats stc;
+    rc = batch_enqueue(bt, bt->cap, stc);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(bt->cap, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(EF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    bt->graph = g;
+    EF_CK(cudaGraphInstantiate(&bt->exec, bt->graph, 0));
+    bt->key = key;
+    return EF_OK;
+}
+
+extern "C" int ef_batch_get_stats(ef_batch* bt, ef_stats* st) {
+    if (!bt || !st) return fail(EF_EINVAL, "NULL argument");
+    *st = ef_stats{};
+    st->kernel_launches = bt->launches;
+    st->logical_branch_dets = bt->logical;
+    return EF_OK;
 }

@@ -272,12 +272,33 @@ static cudaError_t launch_approx_r(const ApproxDev& a, const uint64_t* bits, int
     }
 }
 
+// FP32 minors up to 13 particles per block (the matrix partly lives in local memory)
+template <>
+cudaError_t launch_approx_r<float>(const ApproxDev& a, const uint64_t* bits, int64_t nb, int eta, cudaStream_t s) {
+    switch (eta) {
+        case 1: return launch_approx_eta<float, 1>(a, bits, nb, s);
+        case 2: return launch_approx_eta<float, 2>(a, bits, nb, s);
+        case 3: return launch_approx_eta<float, 3>(a, bits, nb, s);
+        case 4: return launch_approx_eta<float, 4>(a, bits, nb, s);
+        case 5: return launch_approx_eta<float, 5>(a, bits, nb, s);
+        case 6: return launch_approx_eta<float, 6>(a, bits, nb, s);
+        case 7: return launch_approx_eta<float, 7>(a, bits, nb, s);
+        case 8: return launch_approx_eta<float, 8>(a, bits, nb, s);
+        case 9: return launch_approx_eta<float, 9>(a, bits, nb, s);
+        case 10: return launch_approx_eta<float, 10>(a, bits, nb, s);
+        case 11: return launch_approx_eta<float, 11>(a, bits, nb, s);
+        case 12: return launch_approx_eta<float, 12>(a, bits, nb, s);
+        case 13: return launch_approx_eta<float, 13>(a, bits, nb, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_approx(const ApproxDev& a, const uint64_t* bits, int64_t nb, bool fp64, cudaStream_t s,
                           LaunchStats& st) {
     if (nb <= 0) return cudaSuccess;
     int eta = 1;
     for (int B = 0; B < a.nblocks; ++B) eta = std::max(eta, a.blk[B].eta);
-    if (eta > kMaxApproxEta) return cudaErrorInvalidValue;
+    if (eta > (fp64 ? kMaxApproxEta64 : kMaxApproxEta)) return cudaErrorInvalidValue;
     cudaError_t e = fp64 ? launch_approx_r<double>(a, bits, nb, eta, s) : launch_approx_r<float>(a, bits, nb, eta, s);
     st.launches += 1;
     return e;

@@ -174,6 +174,109 @@ cudaError_t launch_exact_lu_f32(const ExactBlockDev& b, const uint64_t* bits, in
     return e;
 }
 
+// ---------------------------------------------------------------- 2a'. FP32 work queue over several circuits
+// Persistent kernel for a batch of circuits whose blocks share eta: every CTA
+// repeatedly takes the next (circuit block, bitstring tile, pattern chunk)
+// item from a device counter, stages that chunk's matrices and factors the
+// minors of its 128 bitstrings exactly as k_exact_lu_f32 does. CTAs leave
+// when the queue is empty (no CTA ever waits for another).
+
+template <int ETA>
+__global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restrict__ q, int nq, int64_t n_items,
+                                                      unsigned long long* __restrict__ head) {
+    extern __shared__ float2 smQ[];
+    __shared__ long long s_item;
+    constexpr int S = ETA | 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(head, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        int lo = 0, hi = nq - 1;  // last entry with item_begin <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (q[mid].item_begin <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const QueueEntry& E = q[lo];
+        const ExactBlockDev& B = E.blk;
+        const int64_t local = item - E.item_begin;
+        const int chunk = (int)(local / E.tiles);
+        const int64_t tile = local - (int64_t)chunk * E.tiles;
+        const int n = B.n;
+        const int Y = 1 << B.c_log2;
+        const float2* src = B.M32 + (size_t)chunk * Y * n * ETA;
+        for (int e = threadIdx.x; e < Y * n * ETA; e += blockDim.x) {
+            const int row = e / ETA, j = e - row * ETA;
+            smQ[row * S + j] = src[e];
+        }
+        __syncthreads();
+        const int64_t b = tile * 128 + threadIdx.x;
+        if (b < E.nb) {
+            int rows[ETA];
+            const bool ok = decode_rows<ETA>(E.bits[2 * b], E.bits[2 * b + 1], B.mask0, B.mask1, rows);
+            for (int t = 0; t < Y; ++t) {
+                const size_t z = (size_t)chunk * Y + t;
+                d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
+                if (ok) {
+                    const float2* Mt = smQ + (size_t)t * n * S;
+                    float2 A[ETA][ETA];
+#pragma unroll
+                    for (int i = 0; i < ETA; ++i) {
+                        const float2* rp = Mt + rows[i] * S;
+#pragma unroll
+                        for (int j = 0; j < ETA; ++j) A[i][j] = rp[j];
+                    }
+                    float er2, zabs2;
+                    const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
+                    res = make_d4((double)det.x, (double)det.y, (double)er2, (double)zabs2);
+                }
+                B.D[z * E.nb + b] = res;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int ETA>
+static cudaError_t launch_queue_eta(const QueueEntry* q, int nq, int64_t n_items, unsigned long long* head,
+                                    size_t smem, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_queue_lu_f32<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) {  // one wave of resident CTAs
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_queue_lu_f32<ETA>, 128, smem)) != cudaSuccess)
+            return e;
+        grid = sms * std::max(1, occ);
+    }
+    k_queue_lu_f32<ETA><<<grid, 128, smem, s>>>(q, nq, n_items, head);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_queue_lu_f32(int eta, const QueueEntry* q, int nq, int64_t n_items, unsigned long long* head,
+                                size_t smem, int grid, cudaStream_t s, LaunchStats& st) {
+    if (n_items <= 0 || nq <= 0) return cudaSuccess;
+    cudaError_t e;
+    switch (eta) {
+        case 1: e = launch_queue_eta<1>(q, nq, n_items, head, smem, grid, s); break;
+        case 2: e = launch_queue_eta<2>(q, nq, n_items, head, smem, grid, s); break;
+        case 3: e = launch_queue_eta<3>(q, nq, n_items, head, smem, grid, s); break;
+        case 4: e = launch_queue_eta<4>(q, nq, n_items, head, smem, grid, s); break;
+        case 5: e = launch_queue_eta<5>(q, nq, n_items, head, smem, grid, s); break;
+        case 6: e = launch_queue_eta<6>(q, nq, n_items, head, smem, grid, s); break;
+        case 7: e = launch_queue_eta<7>(q, nq, n_items, head, smem, grid, s); break;
+        case 8: e = launch_queue_eta<8>(q, nq, n_items, head, smem, grid, s); break;
+        case 9: e = launch_queue_eta<9>(q, nq, n_items, head, smem, grid, s); break;
+        case 10: e = launch_queue_eta<10>(q, nq, n_items, head, smem, grid, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    st.launches += 1;
+    return e;
+}
+
 // ---------------------------------------------------------------- 2b. FP64, thread per minor
 // Thread <-> (pattern, bitstring) work item, consecutive threads on
 // consecutive bitstrings of one pattern; the minor is gathered from the FP64

@@ -18,7 +18,8 @@ constexpr int kMaxModes = 128;
 constexpr int kMaxBlocks = 2;      // independent mode blocks kept factorised
 constexpr int kMaxEtaRows = 32;    // warp-row LU: one lane per minor row
 constexpr int kMaxEtaThread = 10;  // FP32 thread-per-minor LU (registers)
-constexpr int kMaxApproxEta = 8;   // Raw Estimate, thread per trajectory
+constexpr int kMaxApproxEta = 13;    // Raw Estimate, thread per trajectory, FP32 minors
+constexpr int kMaxApproxEta64 = 8;   // FP64 minors
 constexpr int kMaxApproxLayers = 8;
 constexpr int kMaxApproxStored = 64;  // rank-one columns kept per trajectory
 constexpr int kMaxExactPatternBits = 22;  // 2^22 flip patterns per block
@@ -99,6 +100,17 @@ struct ApproxDev {
     ApproxBlockDev blk[kMaxBlocks];
 };
 
+// One (circuit, mode block) of a multi-circuit FP32 LU work queue. Items are
+// (bitstring tile of 128, chunk of patterns); entry e owns items
+// [item_begin, item_begin + tiles * blk.n_chunks).
+struct QueueEntry {
+    ExactBlockDev blk;
+    const uint64_t* bits;
+    int64_t nb;
+    int64_t tiles;
+    int64_t item_begin;
+};
+
 // ---------------------------------------------------------------- adjoint
 
 struct GradDev {
@@ -123,6 +135,11 @@ cudaError_t launch_exact_lu_f32(const ExactBlockDev& b, const uint64_t* bits, in
                                 cudaStream_t s, LaunchStats& st);
 // largest pattern count (log2) a chunk of the FP32 kernel can stage in shared memory
 int exact_f32_chunk_log2(int n, int eta, int r, int64_t nb);
+// Persistent FP32 LU over a work queue of several circuits with the same eta:
+// CTAs take items from *head (reset to 0 before the launch) until none is left.
+cudaError_t launch_queue_lu_f32(int eta, const QueueEntry* entries, int n_entries, int64_t n_items,
+                                unsigned long long* head, size_t smem, int grid, cudaStream_t s,
+                                LaunchStats& st);
 // FP64 minors; thread per minor for eta <= 8, warp-row above
 cudaError_t launch_exact_lu_f64(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
                                 const int* list, const int* list_count, int64_t cap,
