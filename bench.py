@@ -66,7 +66,7 @@ def _oracle_worker(task):
 
 def make_workload(rank: int = 0):
     c, _ = W.config2(0)
-    rng = np.random.default_rng(1002 + 7919 * rank)
+    rng = np.random.default_rng(replica_plan(rank, 1, NB)[0])
     bits = W.spin_sector_bitstrings(16, 8, 8, NB, rng)
     return c, bits
 
@@ -153,6 +153,27 @@ def dist_setup(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def replica_plan(rank: int, world: int, nb: int):
+    """Replicas only: rank r evaluates its own batch of nb bitstrings (seeded by r)
+    whose global indices start at r * nb, so Raw Estimate trajectories never repeat
+    across ranks. Returns (bitstring seed, global index base)."""
+    return 1002 + 7919 * rank, rank * nb
+
+
+def aggregate_timing(local_ms: float, world: int, nb: int, steps: int, dist=None) -> tuple[float, float]:
+    """Whole-job throughput from the slowest rank: (max device ms over ranks,
+    bitstrings of all ranks per second)."""
+    worst = local_ms
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([local_ms], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        worst = float(t.item())
+    return worst, world * nb * steps / (worst / 1e3)
 
 
 def run_reference(args):
@@ -247,12 +268,8 @@ def run_ours(args):
     t_end = time.time()
     clocks = stop_clock_sampler(sampler, clk_path, t_begin, t_end) if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * NB * args.steps / (total_ms / 1e3)
+    total_ms, value = aggregate_timing(sum(step_ms), world, NB, args.steps,
+                                       torch.distributed if world > 1 else None)
     branch_dets = value * 2 ** 16
     last = ef.ef_circuit_get_stats(h)
     p_gpu = d_out.cpu().numpy()
