@@ -409,10 +409,14 @@ def sample_trajectories(circuit, b_index: int, t: int, seed: int, s_start: int =
     return (u < T).astype(np.int8)
 
 
-def raw_estimate(circuit, bitstrings, t: int, seed: int, b_indices=None, return_details: bool = False):
+def raw_estimate(circuit, bitstrings, t: int, seed: int, b_indices=None, return_details: bool = False,
+                 return_scale: bool = False):
     """Raw Estimate for each bitstring; ``b_indices`` are the global bitstring
     indices that key the generator (default 0..nb-1). Returns (p_hat, stderr)
-    or, with ``return_details``, also alpha_hat and the total flip count."""
+    or, with ``return_details``, also alpha_hat and the total flip count; with
+    ``return_scale`` one more array, the mean |Y_i| over the trajectories (the
+    magnitude against which rounding in the terms of the Eq. 11 average is
+    measured)."""
     prep = _Prepared(circuit)
     nb = len(bitstrings)
     if b_indices is None:
@@ -423,6 +427,7 @@ def raw_estimate(circuit, bitstrings, t: int, seed: int, b_indices=None, return_
     p_hat = np.zeros(nb)
     stderr = np.zeros(nb)
     alpha = np.zeros(nb, dtype=np.complex128)
+    scale = np.zeros(nb)
     flips = 0
     step = _chunk_size(prep)
     for i in range(nb):
@@ -442,13 +447,15 @@ def raw_estimate(circuit, bitstrings, t: int, seed: int, b_indices=None, return_
         Y = np.concatenate(Ys) if Ys else np.zeros(0, dtype=np.complex128)
         a = Y.mean()
         alpha[i] = a
+        scale[i] = float(np.abs(Y).mean()) if len(Y) else 0.0
         p_hat[i] = abs(a) ** 2
         if t > 1:
             z = np.real(np.conj(a) * Y)
             stderr[i] = 2.0 * math.sqrt(max(z.var(ddof=1), 0.0) / t)
+    extra = (scale,) if return_scale else ()
     if return_details:
-        return p_hat, stderr, alpha, flips
-    return p_hat, stderr
+        return (p_hat, stderr, alpha, flips) + extra
+    return (p_hat, stderr) + extra
 
 
 def expected_second_moment(circuit, bitstring) -> tuple[complex, float]:

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace ef {
 
 template <typename R> struct V2;
@@ -151,6 +153,35 @@ __device__ __forceinline__ int nth_row(uint64_t w0, uint64_t w1, uint64_t m0, ui
 // sqrt(k+1) u c_k prod_{j != k} |u_jj|; zabs2 is the square of that (0 when no
 // pivot vanished). The elimination steps are a compile-time recursion so every
 // matrix index is a constant and the matrix stays in registers.
+// Rows K+1.. minus l_i times the pivot row K, l_i = A[i][K] / pivot (ip = 1/pivot).
+// In FP32 on sm_100+ each complex update a - l p is two packed FP32x2 FMAs,
+// (a.x, a.y) + (-l.x, -l.x)(p.x, p.y) + (l.y, -l.y)(p.y, p.x).
+template <typename R, int N, int K>
+__device__ __forceinline__ void eliminate(cplx_t<R> (&A)[N][N], cplx_t<R> ip) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    if constexpr (std::is_same<R, float>::value) {
+        float2 psw[N];
+#pragma unroll
+        for (int j = K + 1; j < N; ++j) psw[j] = make_float2(A[K][j].y, A[K][j].x);
+#pragma unroll
+        for (int i = K + 1; i < N; ++i) {
+            const float2 l = cmul(A[i][K], ip);
+            const float2 nl = make_float2(-l.x, -l.x);
+            const float2 ly = make_float2(l.y, -l.y);
+#pragma unroll
+            for (int j = K + 1; j < N; ++j) A[i][j] = __ffma2_rn(ly, psw[j], __ffma2_rn(nl, A[K][j], A[i][j]));
+        }
+        return;
+    }
+#endif
+#pragma unroll
+    for (int i = K + 1; i < N; ++i) {
+        const cplx_t<R> l = cmul(A[i][K], ip);
+#pragma unroll
+        for (int j = K + 1; j < N; ++j) A[i][j] = cfms(A[i][j], l, A[K][j]);
+    }
+}
+
 template <typename R, int N, int K>
 __device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], const R (&cm2)[N], cplx_t<R>& d, bool& odd,
                                         R& er2, R& pz, R& zc, int& nzero) {
@@ -166,14 +197,25 @@ __device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], const R (&cm2)[N],
             p = gt ? i : p;
         }
         odd ^= (p != K);
+        // exchange rows K and p: gather the pivot row by selects, then put the
+        // old row K into slot p (columns >= K only; the rest is never read again)
+        T prow[N];
+#pragma unroll
+        for (int j = K; j < N; ++j) prow[j] = A[K][j];
 #pragma unroll
         for (int i = K + 1; i < N; ++i) {
-            // branch-free swap of rows K and i when i is the pivot row, done on
-            // the bit patterns so that the rows stay in registers
-            const uint32_t msk = 0u - (uint32_t)(p == i);
+            const bool s = (p == i);
 #pragma unroll
-            for (int j = K; j < N; ++j) swap_if(A[K][j], A[i][j], msk);
+            for (int j = K; j < N; ++j) prow[j] = s ? A[i][j] : prow[j];
         }
+#pragma unroll
+        for (int i = K + 1; i < N; ++i) {
+            const bool s = (p == i);
+#pragma unroll
+            for (int j = K; j < N; ++j) A[i][j] = s ? A[K][j] : A[i][j];
+        }
+#pragma unroll
+        for (int j = K; j < N; ++j) A[K][j] = prow[j];
         const T piv = A[K][K];
         d = cmul(d, piv);
         const bool nz = best > R(0);
@@ -183,12 +225,7 @@ __device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], const R (&cm2)[N],
         zc = nz ? zc : R(K + 1) * cm2[K];
         nzero += nz ? 0 : 1;
         const T ip = mk(piv.x * inv, -piv.y * inv);
-#pragma unroll
-        for (int i = K + 1; i < N; ++i) {
-            const T l = cmul(A[i][K], ip);
-#pragma unroll
-            for (int j = K + 1; j < N; ++j) A[i][j] = cfms(A[i][j], l, A[K][j]);
-        }
+        eliminate<R, N, K>(A, ip);
         lu_step<R, N, K + 1>(A, cm2, d, odd, er2, pz, zc, nzero);
     }
 }

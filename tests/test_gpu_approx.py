@@ -3,8 +3,12 @@
 Both sides draw the same trajectories (Philox4x32-10 keyed by seed, global
 bitstring index and trajectory number, integer thresholds), so the estimator
 itself is a deterministic function compared element by element:
-|p_gpu - p_oracle| <= 1e-10 * max(p, p_floor) on the FP64 path and 1e-5 on
-the FP32-minor path; the total number of sampled flips must match exactly."""
+|p_gpu - p_oracle| <= 1e-10 * max(p, p_floor) on the FP64 path. On the
+FP32-minor path each term Y_i of the Eq. 11 average carries a rounding error
+relative to |Y_i|, so the error of alpha scales with M = mean |Y_i| and that of
+p = |alpha|^2 with M^2, which exceeds p where the terms cancel:
+|p_gpu - p_oracle| <= 1e-5 * max(M^2, p_floor). The total number of sampled
+flips must match exactly."""
 import math
 
 import numpy as np
@@ -43,13 +47,16 @@ CASES = [
 def test_approx_matches_oracle_same_trajectories(lib, name, maker, t, prec):
     c, bits = maker()
     seed = 0x1234_5678_9ABC
-    p_ref, se_ref, _, flips_ref = O.raw_estimate(c, bits, t=t, seed=seed, return_details=True)
+    p_ref, se_ref, _, flips_ref, scale = O.raw_estimate(c, bits, t=t, seed=seed, return_details=True,
+                                                         return_scale=True)
     precision = lib.EF_PREC_FP64 if prec == "fp64" else lib.EF_PREC_FP32_MINOR
     p, se, st = run_approx(lib, c, bits, t, seed, precision)
     n = c.n_modes
     floor = 1e-6 / math.comb(n, len(c.occupied_modes()))
-    tol = 1e-10 if prec == "fp64" else 1e-5
-    assert np.max(np.abs(p - p_ref) / np.maximum(p_ref, floor)) <= tol
+    if prec == "fp64":
+        assert np.max(np.abs(p - p_ref) / np.maximum(p_ref, floor)) <= 1e-10
+    else:
+        assert np.max(np.abs(p - p_ref) / np.maximum(scale * scale, floor)) <= 1e-5
     assert np.max(np.abs(se - se_ref) / np.maximum(se_ref, floor)) <= (1e-8 if prec == "fp64" else 1e-3)
     assert st["sampled_flips"] == flips_ref
     assert st["logical_branch_dets"] == len(bits) * t
