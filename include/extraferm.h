@@ -83,8 +83,11 @@ typedef struct {
 typedef enum {
     EF_PREC_FP64 = 0,       /* minors, LU and accumulation in FP64 */
     EF_PREC_FP32_MINOR = 1, /* minors and LU in FP32, branch sum in FP64 */
-    EF_PREC_AUTO = 2        /* FP32 minors; results whose error estimate exceeds
-                               tol are recomputed on the FP64 path (Exact only) */
+    EF_PREC_AUTO = 2        /* FP32 minors; for results whose error estimate exceeds
+                               tol the determinants carrying most of the estimated
+                               error are redone in FP64, then the result is
+                               re-estimated and, if still above tol, all of its
+                               determinants are redone in FP64 (Exact only) */
 } ef_precision;
 
 enum {
@@ -96,13 +99,15 @@ typedef struct {
     int32_t flags;             /* EF_FLAG_* */
     double tol;                /* relative-error target of EF_PREC_AUTO, default 1e-5 */
     int32_t tile_override[4];  /* 0 = automatic; [0] = FP32 Exact sub-branches per chunk (log2);
-                                  [1] = constant K of the FP32 error estimate in tenths (default 30) */
+                                  [1] = constant K of the FP32 error estimate in tenths (default 40) */
 } ef_options;
 
 typedef struct {
     int64_t logical_branch_dets;  /* (bitstring, branch or trajectory) pairs the call evaluated */
     int64_t executed_minor_lus;   /* LU factorizations of minors actually run */
-    int64_t fp64_recomputed;      /* EF_PREC_AUTO: bitstrings redone on the FP64 path */
+    int64_t fp64_recomputed;      /* EF_PREC_AUTO: flagged bitstrings, whose largest-error determinants
+                                     (or, if still above tol, all of them) were redone in FP64; the FP64
+                                     determinants are counted in executed_minor_lus */
     int64_t kernel_launches;      /* kernels this library launched in the call */
     int64_t sampled_flips;        /* Raw Estimate: number of x_j = 1 over all trajectories */
     double max_est_rel_err;       /* largest per-result error estimate of the FP32 path */

@@ -106,6 +106,7 @@ struct HostBlock {
     std::vector<uint32_t> F;       // L x n: flip masks over pattern bits
     std::vector<cd> Omega;         // 2^r_loc: weights of the local gates folded onto patterns
     std::vector<float2> Omega32;   // FP32 copy (error estimate)
+    std::vector<cd> OmegaHat;      // Walsh-Hadamard transform of Omega over the r_loc bits, times 2^-r_loc
     std::vector<uint32_t> sh;      // 2^k_sh: pattern of each shared bit vector
     std::vector<uint32_t> perm, goff;  // shared bit vectors grouped by pattern >> r_loc
     std::vector<uint32_t> coord;       // pattern coordinates of the local, then shared gates
@@ -114,10 +115,11 @@ struct HostBlock {
     std::vector<cd> P;   // tri(L) x n x n
     std::vector<cd> RC;  // L x n x eta
     // device
-    DBuf dS0C, dT, dF, dOmega, dOmega32, dSh, dPerm, dGoff, dM64, dM32, dD, dP64, dP32, dRC64, dRC32, dCols;
+    DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dSh, dPerm, dGoff, dM64, dM32, dD, dMlist, dP64, dP32, dRC64,
+        dRC32, dCols;
     DBuf dCot, dEbar, dTbar, dSbar, dSumT, dSumS, dSumE;
     void release() {
-        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dSh, &dPerm, &dGoff, &dM64, &dM32, &dD, &dP64, &dP32, &dRC64,
+        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dSh, &dPerm, &dGoff, &dM64, &dM32, &dD, &dMlist, &dP64, &dP32, &dRC64,
                         &dRC32, &dCols, &dCot, &dEbar, &dTbar, &dSbar, &dSumT, &dSumS, &dSumE})
             b->release();
     }
@@ -168,7 +170,7 @@ struct ef_circuit {
     ef_stats stats{};
     int64_t last_fp64_list_pending = 0;  // 1 if the FP64 recompute count must be read back
     int64_t last_sub_total = 0;          // sum over blocks of 2^r (minors per bitstring)
-    int* last_recomp = nullptr;          // device counter of the last call's FP64 recomputes
+    unsigned long long* last_recomp = nullptr;          // device counter of the last call's FP64 recomputes
     int last_mode = 0;                   // 1 exact, 2 approx
 
     ~ef_circuit() {
@@ -461,6 +463,7 @@ int prepare(ef_circuit* c) {
                 if ((basis[t][bit >> 6] >> (bit & 63)) & 1ull) B.F[bit] |= 1u << t;
         B.Omega.clear();
         B.Omega32.clear();
+        B.OmegaHat.clear();
         B.sh.clear();
         B.perm.clear();
         B.goff.clear();
@@ -486,6 +489,16 @@ int prepare(ef_circuit* c) {
             B.Omega32.resize(B.Omega.size());
             for (size_t z = 0; z < B.Omega.size(); ++z)
                 B.Omega32[z] = make_float2((float)B.Omega[z].real(), (float)B.Omega[z].imag());
+            // OmegaHat(u) = 2^-r_loc sum_l (-1)^{popcount(u & l)} Omega(l), by butterflies
+            B.OmegaHat = B.Omega;
+            for (size_t h = 1; h < B.OmegaHat.size(); h <<= 1)
+                for (size_t i = 0; i < B.OmegaHat.size(); ++i)
+                    if (!(i & h)) {
+                        const cd a = B.OmegaHat[i], b2 = B.OmegaHat[i | h];
+                        B.OmegaHat[i] = a + b2;
+                        B.OmegaHat[i | h] = a - b2;
+                    }
+            for (cd& v : B.OmegaHat) v = std::ldexp(1.0, -B.r_loc) * v;
             const int ksh_b = c->nblocks == 2 ? k_sh : 0;
             B.sh.assign((size_t)1 << ksh_b, 0u);
             for (uint32_t xs = 0; xs < (1u << ksh_b); ++xs) {
@@ -601,6 +614,7 @@ int upload_tables(ef_circuit* c, cudaStream_t s) {
         EF_CK(upload(B.dF, B.F, s));
         EF_CK(upload(B.dOmega, to_d2(B.Omega), s));
         EF_CK(upload(B.dOmega32, B.Omega32, s));
+        EF_CK(upload(B.dOmegaHat, to_d2(B.OmegaHat), s));
         EF_CK(upload(B.dSh, B.sh, s));
         EF_CK(upload(B.dPerm, B.perm, s));
         EF_CK(upload(B.dGoff, B.goff, s));
@@ -682,22 +696,39 @@ struct ExactBuffers {
     ef::ExactBlockDev blk[ef::kMaxBlocks];
     const double2* Omega[ef::kMaxBlocks];
     const float2* Omega32[ef::kMaxBlocks];
+    const double2* OmegaHat[ef::kMaxBlocks];
     const uint32_t* sh[ef::kMaxBlocks];
     const uint32_t* perm[ef::kMaxBlocks];
     const uint32_t* goff[ef::kMaxBlocks];
     const double2* WS;
     const float2* WS32;
-    int* list;
-    int* count;
-    int* recomp;
+    int* list;   // bitstrings flagged by the FP32 pass
+    int* list2;  // bitstrings still above tol after their listed determinants were redone
+    int* count;  // [0] list size, [1] list2 size, [2 + B] listed determinants of block B
+    int2* mlist[ef::kMaxBlocks];  // (column, pattern) of the determinants to redo in FP64
+    unsigned long long* recomp;   // [0] bitstrings, [1] determinants recomputed in FP64
     int64_t cap;  // bitstrings per batch (row stride of the determinant buffers)
 };
+
+// EF_PREC_AUTO redoes single determinants (rather than whole bitstrings) when
+// the thread-per-minor FP64 kernel covers every block and the combine can hold
+// one variance term per determinant in shared memory.
+bool per_minor_recompute(const ef_circuit* c) {
+    if (c->opt.precision != EF_PREC_AUTO || c->nblocks == 0) return false;
+    int64_t minors = 0;
+    for (int b = 0; b < c->nblocks; ++b) {
+        if (c->blk[b].eta > 8) return false;
+        minors += (int64_t)1 << c->blk[b].r;
+    }
+    return minors <= 8192;
+}
 
 // Bitstrings per batch so that the per-(pattern, bitstring) determinants stay
 // within `budget` bytes.
 int64_t exact_batch(const ef_circuit* c, int64_t nb, size_t budget) {
     size_t per = 0;
-    for (int b = 0; b < c->nblocks; ++b) per += ((size_t)1 << c->blk[b].r) * sizeof(ef::d4);
+    const size_t each = sizeof(ef::d4) + (per_minor_recompute(c) ? sizeof(int2) : 0);
+    for (int b = 0; b < c->nblocks; ++b) per += ((size_t)1 << c->blk[b].r) * each;
     if (per == 0 || nb == 0) return std::max<int64_t>(nb, 1);
     return std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)(budget / per)));
 }
@@ -715,6 +746,21 @@ void exact_block_geometry(const ef_circuit* c, int b, int64_t cap, ef::ExactBloc
     d.mask1 = B.mask[1];
 }
 
+// The transform path of the combine holds both blocks' 2^r values in shared
+// memory (at most 64 KiB) and pays off once the direct sums' 2^(k_sh + r_loc)
+// complex multiply-adds per block exceed the transforms' work.
+bool combine_by_transforms(const ef_circuit* c) {
+    if (c->nblocks != 2) return false;
+    double direct = 0.0, wht = 0.0;
+    for (int b = 0; b < 2; ++b) {
+        const HostBlock& B = c->blk[b];
+        if (B.r_loc < 1 || B.r > 11) return false;
+        direct += 4.0 * std::ldexp(1.0, (int)c->shared_gates.size() + B.r_loc);
+        wht += std::ldexp(1.0, B.r) * (4.0 * B.r_loc + 4.0);
+    }
+    return wht < direct;
+}
+
 ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
     ef::ExactCombineDev cm{};
     cm.nblocks = c->nblocks;
@@ -730,12 +776,17 @@ ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
         cm.D[b] = eb.blk[b].D;
         cm.Omega[b] = eb.Omega[b];
         cm.Omega32[b] = eb.Omega32[b];
+        cm.OmegaHat[b] = eb.OmegaHat[b];
         cm.s[b] = eb.sh[b];
         cm.perm[b] = eb.perm[b];
         cm.goff[b] = eb.goff[b];
     }
     cm.WS = eb.WS;
     cm.WS32 = eb.WS32;
+    cm.wht = combine_by_transforms(c) ? 1 : 0;
+    cm.minors = 0;
+    for (int b = 0; b < c->nblocks; ++b) cm.minors += (int64_t)1 << c->blk[b].r;
+    cm.mcount = eb.count + 2;
     cm.tol = c->opt.tol;
     cm.p_floor = c->p_floor;
     return cm;
@@ -787,20 +838,45 @@ int exact_enqueue_lu(ef_circuit* c, const ExactBuffers& eb, const uint64_t* bits
     return EF_OK;
 }
 
-// combine, and under EF_PREC_AUTO the FP64 recompute of flagged results
+// combine, and under EF_PREC_AUTO the FP64 recompute of flagged results:
+// per determinant when eb.mlist is set (FP32 pass -> listed determinants in
+// FP64 -> combine of the flagged bitstrings with a new estimate -> whole
+// bitstrings still above tol in FP64 -> their combine), else per bitstring.
 int exact_enqueue_combine(ef_circuit* c, const ExactBuffers& eb, ef::ExactCombineDev cm, const uint64_t* bits,
                           int64_t nbb, double* out, double* err, cudaStream_t s, ef::LaunchStats& st) {
     const bool autofix = c->opt.precision == EF_PREC_AUTO;
-    if (autofix) EF_CK(cudaMemsetAsync(eb.count, 0, sizeof(int), s));
     cm.err_coef = fp32_err_coef(c);
-    cm.recomputed_total = nullptr;
-    EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, nullptr, nullptr, out, err, autofix ? eb.list : nullptr,
-                                   autofix ? eb.count : nullptr, s, st));
-    if (autofix) {
+    if (!autofix) {
+        EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, nullptr, nullptr, out, err, nullptr, nullptr, s, st));
+        return EF_OK;
+    }
+    const bool per_minor = eb.mlist[0] != nullptr;
+    EF_CK(cudaMemsetAsync(eb.count, 0, 4 * sizeof(int), s));
+    for (int b = 0; b < c->nblocks; ++b) cm.mlist[b] = per_minor ? eb.mlist[b] : nullptr;
+    EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, nullptr, nullptr, out, err, eb.list, eb.count, s, st));
+    for (int b = 0; b < c->nblocks; ++b) cm.mlist[b] = nullptr;
+    cm.recomp = eb.recomp;
+    if (per_minor) {
+        for (int b = 0; b < c->nblocks; ++b)
+            EF_CK(ef::launch_exact_lu_f64_minors(eb.blk[b], bits, eb.mlist[b], eb.count + 2 + b, nbb, s, st));
+        ef::ExactCombineDev chk = cm;
+        chk.col_by_index = 1;
+        chk.count_bits = 1;
+        chk.count_minors = 1;
+        EF_CK(ef::launch_exact_combine(chk, bits, nbb, nbb, eb.list, eb.count, out, err, eb.list2, eb.count + 1, s,
+                                       st));
+        for (int b = 0; b < c->nblocks; ++b)
+            EF_CK(ef::launch_exact_lu_f64(eb.blk[b], bits, nbb, eb.list2, eb.count + 1, nbb, s, st));
+        cm.err_coef = 0.0;
+        cm.count_full = 1;
+        EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, eb.list2, eb.count + 1, out, err, nullptr, nullptr, s,
+                                       st));
+    } else {
         for (int b = 0; b < c->nblocks; ++b)
             EF_CK(ef::launch_exact_lu_f64(eb.blk[b], bits, nbb, eb.list, eb.count, nbb, s, st));
         cm.err_coef = 0.0;
-        cm.recomputed_total = eb.recomp;
+        cm.count_bits = 1;
+        cm.count_full = 1;
         EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, eb.list, eb.count, out, err, nullptr, nullptr, s, st));
     }
     return EF_OK;
@@ -814,7 +890,7 @@ int run_exact(ef_circuit* c, const ExactBuffers& eb, const uint64_t* d_bits, int
     if (rc) return rc;
     const ef::ExactCombineDev cm = make_combine(c, eb);
     if (autofix) {
-        EF_CK(cudaMemsetAsync(eb.recomp, 0, sizeof(int), s));
+        EF_CK(cudaMemsetAsync(eb.recomp, 0, 2 * sizeof(unsigned long long), s));
         c->last_recomp = eb.recomp;
         c->last_fp64_list_pending = 1;
     }
@@ -859,18 +935,26 @@ int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
         d.D = B.dD.as<ef::d4>();
         eb.Omega[b] = B.dOmega.as<double2>();
         eb.Omega32[b] = B.dOmega32.as<float2>();
+        eb.OmegaHat[b] = B.dOmegaHat.as<double2>();
         eb.sh[b] = B.dSh.as<uint32_t>();
         eb.perm[b] = B.dPerm.as<uint32_t>();
         eb.goff[b] = B.dGoff.as<uint32_t>();
     }
     eb.WS = c->dWS.as<double2>();
     eb.WS32 = c->dWS32.as<float2>();
-    EF_CK(c->dList.ensure((size_t)cap * sizeof(int)));
-    EF_CK(c->dListCount.ensure(sizeof(int)));
-    EF_CK(c->dRecomp.ensure(sizeof(int)));
+    EF_CK(c->dList.ensure(2 * (size_t)cap * sizeof(int)));
+    EF_CK(c->dListCount.ensure(4 * sizeof(int)));
+    EF_CK(c->dRecomp.ensure(2 * sizeof(unsigned long long)));
     eb.list = c->dList.as<int>();
+    eb.list2 = eb.list + cap;
     eb.count = c->dListCount.as<int>();
-    eb.recomp = c->dRecomp.as<int>();
+    eb.recomp = c->dRecomp.as<unsigned long long>();
+    if (per_minor_recompute(c))
+        for (int b = 0; b < c->nblocks; ++b) {
+            HostBlock& B = c->blk[b];
+            EF_CK(B.dMlist.ensure(((size_t)1 << B.r) * (size_t)cap * sizeof(int2)));
+            eb.mlist[b] = B.dMlist.as<int2>();
+        }
     return EF_OK;
 }
 
@@ -1456,10 +1540,10 @@ int ef_circuit_get_stats(ef_circuit* c, ef_stats* st) {
         c->stats.dominant_kernel_ms = ms;
     }
     if (c->last_mode == 1 && c->last_fp64_list_pending && c->last_recomp) {
-        int cnt = 0;
-        EF_CK(cudaMemcpy(&cnt, c->last_recomp, sizeof(int), cudaMemcpyDeviceToHost));
-        c->stats.fp64_recomputed = cnt;
-        c->stats.executed_minor_lus += (int64_t)cnt * c->last_sub_total;
+        unsigned long long cnt[2] = {0, 0};
+        EF_CK(cudaMemcpy(cnt, c->last_recomp, sizeof(cnt), cudaMemcpyDeviceToHost));
+        c->stats.fp64_recomputed = (int64_t)cnt[0];
+        c->stats.executed_minor_lus += (int64_t)cnt[1];
         c->last_fp64_list_pending = 0;
     }
     if (c->last_mode == 2 && c->dCounters.p) {
@@ -1556,6 +1640,7 @@ size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* bas
         d.F = cv.take<uint32_t>(B.F.size());
         eb.Omega[b] = cv.take<double2>(B.Omega.size());
         eb.Omega32[b] = cv.take<float2>(B.Omega32.size());
+        eb.OmegaHat[b] = cv.take<double2>(B.OmegaHat.size());
         eb.sh[b] = cv.take<uint32_t>(B.sh.size());
         eb.perm[b] = cv.take<uint32_t>(B.perm.size());
         eb.goff[b] = cv.take<uint32_t>(B.goff.size());
@@ -1566,8 +1651,12 @@ size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* bas
     eb.WS = cv.take<double2>(c->WS.size());
     eb.WS32 = cv.take<float2>(c->WS32.size());
     eb.list = cv.take<int>((size_t)eb.cap);
-    eb.count = cv.take<int>(1);
-    eb.recomp = cv.take<int>(1);
+    eb.list2 = cv.take<int>((size_t)eb.cap);
+    eb.count = cv.take<int>(4);
+    eb.recomp = cv.take<unsigned long long>(2);
+    if (per_minor_recompute(c))
+        for (int b = 0; b < c->nblocks; ++b)
+            eb.mlist[b] = cv.take<int2>(((size_t)1 << c->blk[b].r) * (size_t)eb.cap);
     return (cv.off + 255) & ~(size_t)255;
 }
 
@@ -1631,6 +1720,7 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
         EF_CK(copy_in(d.F, B.F, s));
         EF_CK(copy_in_c(eb.Omega[b], B.Omega.data(), B.Omega.size(), s));
         EF_CK(copy_in(eb.Omega32[b], B.Omega32, s));
+        EF_CK(copy_in_c(eb.OmegaHat[b], B.OmegaHat.data(), B.OmegaHat.size(), s));
         EF_CK(copy_in(eb.sh[b], B.sh, s));
         EF_CK(copy_in(eb.perm[b], B.perm, s));
         EF_CK(copy_in(eb.goff[b], B.goff, s));
@@ -1757,7 +1847,8 @@ int batch_enqueue(ef_batch* bt, cudaStream_t s, ef::LaunchStats& st) {
         ef_circuit* c = bt->cs[i];
         int rc = exact_enqueue_build(c, it.eb, s, st);
         if (rc) return rc;
-        if (c->opt.precision == EF_PREC_AUTO) EF_CK(cudaMemsetAsync(it.eb.recomp, 0, sizeof(int), s));
+        if (c->opt.precision == EF_PREC_AUTO)
+            EF_CK(cudaMemsetAsync(it.eb.recomp, 0, 2 * sizeof(unsigned long long), s));
     }
     for (size_t k = 0; k < bt->classes.size(); ++k) {
         int rc = batch_launch_queue(bt, (int)k, s, st);

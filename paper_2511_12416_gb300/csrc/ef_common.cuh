@@ -251,6 +251,56 @@ __device__ __forceinline__ cplx_t<R> lu_det_regs(cplx_t<R> (&A)[N][N], R& er2, R
     return odd ? mk(-d.x, -d.y) : d;
 }
 
+// The same elimination without the rounding-error proxy: for results that
+// are final (FP64) rather than estimated.
+template <typename R, int N, int K>
+__device__ __forceinline__ void lu_step_plain(cplx_t<R> (&A)[N][N], cplx_t<R>& d, bool& odd) {
+    if constexpr (K < N) {
+        using T = cplx_t<R>;
+        R best = abs2(A[K][K]);
+        int p = K;
+#pragma unroll
+        for (int i = K + 1; i < N; ++i) {
+            const R m = abs2(A[i][K]);
+            const bool gt = m > best;
+            best = gt ? m : best;
+            p = gt ? i : p;
+        }
+        odd ^= (p != K);
+        T prow[N];
+#pragma unroll
+        for (int j = K; j < N; ++j) prow[j] = A[K][j];
+#pragma unroll
+        for (int i = K + 1; i < N; ++i) {
+            const bool s = (p == i);
+#pragma unroll
+            for (int j = K; j < N; ++j) prow[j] = s ? A[i][j] : prow[j];
+        }
+#pragma unroll
+        for (int i = K + 1; i < N; ++i) {
+            const bool s = (p == i);
+#pragma unroll
+            for (int j = K; j < N; ++j) A[i][j] = s ? A[K][j] : A[i][j];
+        }
+#pragma unroll
+        for (int j = K; j < N; ++j) A[K][j] = prow[j];
+        const T piv = A[K][K];
+        d = cmul(d, piv);
+        const R inv = best > R(0) ? recip(best) : R(0);
+        const T ip = mk(piv.x * inv, -piv.y * inv);
+        eliminate<R, N, K>(A, ip);
+        lu_step_plain<R, N, K + 1>(A, d, odd);
+    }
+}
+
+template <typename R, int N>
+__device__ __forceinline__ cplx_t<R> lu_det_plain(cplx_t<R> (&A)[N][N]) {
+    cplx_t<R> d = mk(R(1), R(0));
+    bool odd = false;
+    lu_step_plain<R, N, 0>(A, d, odd);
+    return odd ? mk(-d.x, -d.y) : d;
+}
+
 // Warp-row LU: a group of G lanes (G a power of two, 1 < G <= 32) holds one
 // eta x eta minor, lane r of the group owning row r (rows >= eta are padding).
 // The rows never move: at step k the group finds the pivot row p (largest

@@ -304,12 +304,65 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const ui
             for (int i = 0; i < ETA; ++i)
 #pragma unroll
                 for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
-            double er2, zabs2;
-            const double2 det = lu_det_regs<double, ETA>(A, er2, zabs2);
-            res = make_d4(det.x, det.y, er2, zabs2);
+            const double2 det = lu_det_plain<double, ETA>(A);
+            res = make_d4(det.x, det.y, 0.0, 0.0);
         }
         B.D[(size_t)z * stride + pos] = res;
     }
+}
+
+// Thread <-> one listed determinant (bitstring column, pattern z): redone in
+// FP64 in place, with zero error terms.
+template <int ETA>
+__global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B, const uint64_t* __restrict__ bits,
+                                                       const int2* __restrict__ mlist,
+                                                       const int* __restrict__ mcount, int64_t stride) {
+    const int64_t count = *mcount;
+    const int n = B.n;
+    for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < count;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = mlist[item];
+        const int64_t pos = e.x;
+        const int z = e.y;
+        int rows[ETA];
+        d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
+        if (decode_rows<ETA>(bits[2 * pos], bits[2 * pos + 1], B.mask0, B.mask1, rows)) {
+            const double2* Mz = B.M64 + (size_t)z * n * ETA;
+            double2 A[ETA][ETA];
+#pragma unroll
+            for (int i = 0; i < ETA; ++i)
+#pragma unroll
+                for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
+            const double2 det = lu_det_plain<double, ETA>(A);
+            res = make_d4(det.x, det.y, 0.0, 0.0);
+        }
+        B.D[(size_t)z * stride + pos] = res;
+    }
+}
+
+template <int ETA>
+static cudaError_t launch_f64m_eta(const ExactBlockDev& b, const uint64_t* bits, const int2* mlist,
+                                   const int* mcount, int64_t stride, cudaStream_t s) {
+    k_exact_lu_f64m<ETA><<<152 * 8, 128, 0, s>>>(b, bits, mlist, mcount, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_lu_f64_minors(const ExactBlockDev& b, const uint64_t* bits, const int2* mlist,
+                                       const int* mcount, int64_t stride, cudaStream_t s, LaunchStats& st) {
+    cudaError_t e;
+    switch (b.eta) {
+        case 1: e = launch_f64m_eta<1>(b, bits, mlist, mcount, stride, s); break;
+        case 2: e = launch_f64m_eta<2>(b, bits, mlist, mcount, stride, s); break;
+        case 3: e = launch_f64m_eta<3>(b, bits, mlist, mcount, stride, s); break;
+        case 4: e = launch_f64m_eta<4>(b, bits, mlist, mcount, stride, s); break;
+        case 5: e = launch_f64m_eta<5>(b, bits, mlist, mcount, stride, s); break;
+        case 6: e = launch_f64m_eta<6>(b, bits, mlist, mcount, stride, s); break;
+        case 7: e = launch_f64m_eta<7>(b, bits, mlist, mcount, stride, s); break;
+        case 8: e = launch_f64m_eta<8>(b, bits, mlist, mcount, stride, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    st.launches += 1;
+    return e;
 }
 
 template <int ETA>
@@ -430,23 +483,42 @@ cudaError_t launch_exact_lu_f64(const ExactBlockDev& b, const uint64_t* bits, in
 // C_B(z) = sum_{x_sh} w_sh(x_sh) Omega_B(z ^ s_B(x_sh)) A_other(x_sh), and
 // rounding errors of different determinants are independent, so
 // Var(d amp) = (K u)^2 sum_{B,z} |C_B(z)|^2 (|det|^2 er2 + zabs2).
+//
+// With pattern coordinates z = (h, l), l the r_loc bits of the local gates,
+// A_B(x_sh) = F_B(s_B(x_sh)) where F_B(h, m) = sum_l Omega_B(l) det_B(h, l ^ m)
+// is an XOR convolution over l. When the 2^r values of both blocks fit in
+// shared memory (C.wht) it is taken as a Walsh-Hadamard transform over l, a
+// product with the transformed weights and the inverse transform:
+// 4 r_loc 2^r real additions and 2^r complex products per block instead of
+// 2^(k_sh + r_loc) complex multiply-adds.
 
 __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-    red[threadIdx.x] = v;
-    __syncthreads();
+__device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-    for (int off = NT / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-        __syncthreads();
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// One stage of an in-place Walsh-Hadamard transform over bit j of F's index
+// (n/2 butterflies), optionally followed by the product with W[index & lm].
+__device__ __forceinline__ void wht_stage(double2* F, int half, int j, const double2* W, uint32_t lm, int tid,
+                                          int nt) {
+    for (int q = tid; q < half; q += nt) {
+        const int i0 = ((q >> j) << (j + 1)) | (q & ((1 << j) - 1));
+        const int i1 = i0 | (1 << j);
+        const double2 a = F[i0], b = F[i1];
+        double2 u = make_double2(a.x + b.x, a.y + b.y);
+        double2 v = make_double2(a.x - b.x, a.y - b.y);
+        if (W) {
+            u = cmul_d(u, W[i0 & lm]);
+            v = cmul_d(v, W[i1 & lm]);
+        }
+        F[i0] = u;
+        F[i1] = v;
     }
-    const double r = red[0];
-    __syncthreads();
-    return r;
 }
 
 __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const uint64_t* __restrict__ bits,
@@ -455,15 +527,34 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                                                        double* __restrict__ err, int* __restrict__ append_list,
                                                        int* __restrict__ append_count) {
     constexpr int NT = 256;
-    extern __shared__ float2 smA32[];  // FP32 copies of A_0[2^k_sh], A_1[2^k_sh] for the error estimate
-    __shared__ double red[NT];
+    constexpr int NW = NT / 32;
+    // dynamic shared memory: [F_0 (2^r_0), F_1 (2^r_1) double2 when C.wht]
+    // [FP32 copies of A_0, A_1 (2^k_sh each) for the error estimate]
+    // [the variance term of every determinant (2^r_0 + 2^r_1 floats) when
+    //  listing the determinants to redo in FP64]
+    extern __shared__ double2 smDyn[];
+    __shared__ double red[3 * NW];
+    __shared__ double s_theta;
+    const int nsh = 1 << C.k_sh;
+    const int nF = C.wht ? (1 << C.r[0]) + (1 << C.r[1]) : 0;
+    double2* F0 = smDyn;
+    double2* F1 = smDyn + (C.wht ? (1 << C.r[0]) : 0);
+    float2* smA32 = reinterpret_cast<float2*>(smDyn + nF);
+    float* smV = reinterpret_cast<float*>(smA32 + 2 * nsh);
     const int tid = threadIdx.x;
     const int64_t count = list ? (int64_t)(*list_count) : nb;
-    if (list && C.recomputed_total && blockIdx.x == 0 && tid == 0) atomicAdd(C.recomputed_total, (int)count);
-    const int nsh = 1 << C.k_sh;
+    if (C.recomp && blockIdx.x == 0 && tid == 0) {
+        if (C.count_bits) atomicAdd(&C.recomp[0], (unsigned long long)count);
+        if (C.count_full) atomicAdd(&C.recomp[1], (unsigned long long)count * (unsigned long long)C.minors);
+        if (C.count_minors)
+            for (int B = 0; B < C.nblocks; ++B) atomicAdd(&C.recomp[1], (unsigned long long)C.mcount[B]);
+    }
     const bool want_err = C.err_coef > 0.0;
+    const bool emit = want_err && !list && C.mlist[0] != nullptr;
+    const int voff1 = C.nblocks == 2 ? (1 << C.r[0]) : 0;
     for (int64_t pos = blockIdx.x; pos < count; pos += gridDim.x) {
         const int64_t b = list ? (int64_t)list[pos] : pos;
+        const int64_t col = C.col_by_index ? b : pos;  // column of D holding this bitstring's determinants
         const uint64_t w0 = bits[2 * b], w1 = bits[2 * b + 1];
         bool ok = ((w0 & C.inactive0) == 0) && ((w1 & C.inactive1) == 0);
         for (int B = 0; B < C.nblocks; ++B)
@@ -482,11 +573,48 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
             // amp = sum_z Omega(z) det(z); C(z) = Omega(z)
             const int nz = 1 << C.r[0];
             for (int z = tid; z < nz; z += NT) {
-                const d4 v = C.D[0][(size_t)z * stride + pos];
+                const d4 v = C.D[0][(size_t)z * stride + col];
                 const double2 w = C.Omega[0][z];
                 ar = fma(w.x, v.x, fma(-w.y, v.y, ar));
                 ai = fma(w.x, v.y, fma(w.y, v.x, ai));
-                if (want_err) var = fma(w.x * w.x + w.y * w.y, fma(v.x * v.x + v.y * v.y, v.z, v.w), var);
+                if (want_err) {
+                    const double vt = (w.x * w.x + w.y * w.y) * fma(v.x * v.x + v.y * v.y, v.z, v.w);
+                    var += vt;
+                    if (emit) smV[z] = (float)vt;
+                }
+            }
+        } else if (C.wht) {
+            for (int B = 0; B < 2; ++B) {
+                double2* FB = B ? F1 : F0;
+                const int nz = 1 << C.r[B];
+                for (int z = tid; z < nz; z += NT) {
+                    const d4 v = C.D[B][(size_t)z * stride + col];
+                    FB[z] = make_double2(v.x, v.y);
+                }
+            }
+            __syncthreads();
+            // forward transform (the last stage also multiplies by the transformed
+            // weights, which carry the inverse's 2^-r_loc), then the inverse
+            const int rl = max(C.r_loc[0], C.r_loc[1]);
+            for (int pass = 0; pass < 2; ++pass)
+                for (int j = 0; j < rl; ++j) {
+                    for (int B = 0; B < 2; ++B) {
+                        if (j >= C.r_loc[B]) continue;
+                        const bool mul = pass == 0 && j == C.r_loc[B] - 1;
+                        wht_stage(B ? F1 : F0, 1 << (C.r[B] - 1), j, mul ? C.OmegaHat[B] : nullptr,
+                                  (1u << C.r_loc[B]) - 1u, tid, NT);
+                    }
+                    __syncthreads();
+                }
+            for (int xs = tid; xs < nsh; xs += NT) {
+                const double2 a0 = F0[C.s[0][xs]], a1 = F1[C.s[1][xs]];
+                if (want_err) {
+                    smA32[xs] = make_float2((float)a0.x, (float)a0.y);
+                    smA32[nsh + xs] = make_float2((float)a1.x, (float)a1.y);
+                }
+                const double2 t = cmul_d(C.WS[xs], cmul_d(a0, a1));
+                ar += t.x;
+                ai += t.y;
             }
         } else {
             const int nl0 = 1 << C.r_loc[0], nl1 = 1 << C.r_loc[1];
@@ -497,70 +625,118 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                     const int nl = B == 0 ? nl0 : nl1;
                     double sx = 0.0, sy = 0.0;
                     for (int zl = 0; zl < nl; ++zl) {
-                        const d4 v = C.D[B][(size_t)(zl ^ sB) * stride + pos];
+                        const d4 v = C.D[B][(size_t)(zl ^ sB) * stride + col];
                         const double2 w = C.Omega[B][zl];
                         sx = fma(w.x, v.x, fma(-w.y, v.y, sx));
                         sy = fma(w.x, v.y, fma(w.y, v.x, sy));
                     }
                     a[B] = make_double2(sx, sy);
-                    if (want_err)
-                        smA32[B * nsh + xs] = make_float2((float)sx, (float)sy);
+                    if (want_err) smA32[B * nsh + xs] = make_float2((float)sx, (float)sy);
                 }
                 const double2 t = cmul_d(C.WS[xs], cmul_d(a[0], a[1]));
                 ar += t.x;
                 ai += t.y;
             }
-            if (want_err) {
-                // the estimate needs no FP64: coefficients in FP32
-                __syncthreads();
-                for (int B = 0; B < 2; ++B) {
-                    const int nz = 1 << C.r[B];
-                    const uint32_t lmask = (1u << C.r_loc[B]) - 1u;
-                    const float2* Aoth = smA32 + (1 - B) * nsh;
-                    for (int z = tid; z < nz; z += NT) {
-                        const uint32_t h = (uint32_t)z >> C.r_loc[B];
-                        float cx = 0.f, cy = 0.f;
-                        for (uint32_t g = C.goff[B][h]; g < C.goff[B][h + 1]; ++g) {
-                            const uint32_t xs = C.perm[B][g];
-                            const uint32_t zl = ((uint32_t)z ^ C.s[B][xs]) & lmask;
-                            const float2 t = cmul(C.WS32[xs], cmul(C.Omega32[B][zl], Aoth[xs]));
-                            cx += t.x;
-                            cy += t.y;
-                        }
-                        const d4 v = C.D[B][(size_t)z * stride + pos];
-                        const double c2 = (double)cx * cx + (double)cy * cy;
-                        var = fma(c2, fma(v.x * v.x + v.y * v.y, v.z, v.w), var);
+        }
+        // amplitude: warp butterflies, then the warps' partial sums in a fixed
+        // order (every thread forms the same total)
+        ar = warp_sum(ar);
+        ai = warp_sum(ai);
+        if ((tid & 31) == 0) {
+            red[tid >> 5] = ar;
+            red[NW + (tid >> 5)] = ai;
+        }
+        __syncthreads();
+        ar = red[0];
+        ai = red[NW];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) {
+            ar += red[w];
+            ai += red[NW + w];
+        }
+        const double p = ar * ar + ai * ai;
+        if (want_err && C.nblocks == 2) {
+            // the estimate needs no FP64: coefficients in FP32
+            for (int B = 0; B < 2; ++B) {
+                const int nz = 1 << C.r[B];
+                const uint32_t lmask = (1u << C.r_loc[B]) - 1u;
+                const float2* Aoth = smA32 + (1 - B) * nsh;
+                for (int z = tid; z < nz; z += NT) {
+                    const uint32_t h = (uint32_t)z >> C.r_loc[B];
+                    float cx = 0.f, cy = 0.f;
+                    for (uint32_t g = C.goff[B][h]; g < C.goff[B][h + 1]; ++g) {
+                        const uint32_t xs = C.perm[B][g];
+                        const uint32_t zl = ((uint32_t)z ^ C.s[B][xs]) & lmask;
+                        const float2 t = cmul(C.WS32[xs], cmul(C.Omega32[B][zl], Aoth[xs]));
+                        cx += t.x;
+                        cy += t.y;
                     }
+                    const d4 v = C.D[B][(size_t)z * stride + col];
+                    const double c2 = (double)cx * cx + (double)cy * cy;
+                    const double vt = c2 * fma(v.x * v.x + v.y * v.y, v.z, v.w);
+                    var += vt;
+                    if (emit) smV[B * voff1 + z] = (float)vt;
                 }
             }
         }
-        ar = block_sum<NT>(ar, red);
-        ai = block_sum<NT>(ai, red);
-        if (want_err) var = block_sum<NT>(var, red);
+        var = warp_sum(var);
+        if ((tid & 31) == 0) red[2 * NW + (tid >> 5)] = var;
+        __syncthreads();
         if (tid == 0) {
-            const double p = ar * ar + ai * ai;
-            const double dabs = 2.0 * sqrt(p) * C.err_coef * sqrt(var);
+            var = red[2 * NW];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) var += red[2 * NW + w];
+            const double sp = sqrt(p);
+            const double dabs = 2.0 * sp * C.err_coef * sqrt(var);
             const double e = dabs / fmax(p, C.p_floor);
             out[b] = p;
             if (list) {
                 if (err) err[b] = -fabs(err[b]);
-            } else {
-                if (err) err[b] = e;
-                if (append_list && e > C.tol) {
-                    const int idx = atomicAdd(append_count, 1);
-                    append_list[idx] = (int)b;
-                }
+            } else if (err) {
+                err[b] = e;
             }
+            const bool flag = append_list && e > C.tol;
+            if (flag) {
+                const int idx = atomicAdd(append_count, 1);
+                append_list[idx] = (int)b;
+            }
+            if (emit) {
+                // variance at which the estimate equals tol; determinants whose term
+                // exceeds half of it shared over all of them are redone, so the
+                // terms left cannot sum past half of it
+                const double vt = C.tol * fmax(p, C.p_floor) / (2.0 * sp * C.err_coef);
+                s_theta = flag ? 0.5 * vt * vt / (double)C.minors : -1.0;
+            }
+        }
+        if (emit) {
+            __syncthreads();
+            const double theta = s_theta;
+            if (theta >= 0.0)
+                for (int B = 0; B < C.nblocks; ++B) {
+                    const int nz = 1 << C.r[B];
+                    for (int z = tid; z < nz; z += NT)
+                        if ((double)smV[B * voff1 + z] > theta) {
+                            const int idx = atomicAdd(&C.mcount[B], 1);
+                            C.mlist[B][idx] = make_int2((int)pos, z);
+                        }
+                }
         }
         __syncthreads();
     }
+}
+
+size_t exact_combine_smem(const ExactCombineDev& c) {
+    size_t smem = (size_t)2 * ((size_t)1 << c.k_sh) * sizeof(float2);
+    if (c.wht) smem += (((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1])) * sizeof(double2);
+    if (c.mlist[0]) smem += (size_t)c.minors * sizeof(float);
+    return smem;
 }
 
 cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits, int64_t nb, int64_t stride,
                                  const int* list, const int* list_count, double* out, double* err, int* append_list,
                                  int* append_count, cudaStream_t s, LaunchStats& st) {
     if (nb <= 0) return cudaSuccess;
-    const size_t smem = (size_t)2 * ((size_t)1 << c.k_sh) * sizeof(float2);
+    const size_t smem = exact_combine_smem(c);
     cudaError_t e = cudaFuncSetAttribute(k_exact_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, 152 * 16));

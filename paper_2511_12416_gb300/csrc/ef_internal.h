@@ -65,10 +65,21 @@ struct ExactCombineDev {
     const uint32_t* goff[kMaxBlocks];  // 2^(r - r_loc) + 1 group offsets
     const double2* WS;                 // 2^k_sh weights of the shared gates
     const float2* Omega32[kMaxBlocks]; // FP32 copies for the error estimate
+    const double2* OmegaHat[kMaxBlocks];  // 2^r_loc: Walsh-Hadamard transform of Omega times 2^-r_loc
+    int wht;                           // 1: XOR convolutions by transforms in shared memory
     const float2* WS32;
     double err_coef;                   // K u32 (FP32 path), 0 for FP64
     double tol, p_floor;
-    int* recomputed_total;             // list mode: accumulates the list sizes
+    int64_t minors;                    // determinants per bitstring, sum over blocks of 2^r
+    int col_by_index;                  // D column of a listed bitstring: its index (1) or list position (0)
+    // EF_PREC_AUTO: when flagging a result, list its determinants whose
+    // variance terms are large (mlist[B] entries (column, z), counts in mcount)
+    int2* mlist[kMaxBlocks];
+    int* mcount;
+    // recompute counters: [0] bitstrings, [1] FP64 determinants; the launch adds
+    // the list size (count_bits), list size x minors (count_full), sum of mcount (count_minors)
+    unsigned long long* recomp;
+    int count_bits, count_full, count_minors;
 };
 
 // ---------------------------------------------------------------- Raw Estimate
@@ -144,9 +155,13 @@ cudaError_t launch_queue_lu_f32(int eta, const QueueEntry* entries, int n_entrie
 cudaError_t launch_exact_lu_f64(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
                                 const int* list, const int* list_count, int64_t cap,
                                 cudaStream_t s, LaunchStats& st);
+// FP64 redo of the listed determinants mlist[0..*mcount) in place (eta <= 8)
+cudaError_t launch_exact_lu_f64_minors(const ExactBlockDev& b, const uint64_t* bits, const int2* mlist,
+                                       const int* mcount, int64_t stride, cudaStream_t s, LaunchStats& st);
 cudaError_t launch_exact_lu_rows(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
                                  const int* list, const int* list_count, int64_t cap,
                                  bool fp64, cudaStream_t s, LaunchStats& st);
+size_t exact_combine_smem(const ExactCombineDev& c);
 cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits, int64_t nb, int64_t stride,
                                  const int* list, const int* list_count, double* out, double* err,
                                  int* append_list, int* append_count, cudaStream_t s, LaunchStats& st);
