@@ -89,6 +89,16 @@ cudaError_t upload(DBuf& d, const std::vector<T>& h, cudaStream_t s) {
     return cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
 }
 
+// complex values as float pairs (re hi, re lo, im hi, im lo), hi + lo = value to ~48 bits
+std::vector<float4> to_ff(const std::vector<cd>& v) {
+    std::vector<float4> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        const float rh = (float)v[i].real(), ih = (float)v[i].imag();
+        o[i] = make_float4(rh, (float)(v[i].real() - (double)rh), ih, (float)(v[i].imag() - (double)ih));
+    }
+    return o;
+}
+
 struct HostBlock {
     int n = 0, eta = 0, L = 0;
     uint64_t mask[2] = {0, 0};
@@ -107,6 +117,7 @@ struct HostBlock {
     std::vector<cd> Omega;         // 2^r_loc: weights of the local gates folded onto patterns
     std::vector<float2> Omega32;   // FP32 copy (error estimate)
     std::vector<cd> OmegaHat;      // Walsh-Hadamard transform of Omega over the r_loc bits, times 2^-r_loc
+    std::vector<float4> OmegaHatFF;  // the same as float pairs
     std::vector<uint32_t> sh;      // 2^k_sh: pattern of each shared bit vector
     std::vector<uint32_t> perm, goff;  // shared bit vectors grouped by pattern >> r_loc
     std::vector<uint32_t> coord;       // pattern coordinates of the local, then shared gates
@@ -115,11 +126,11 @@ struct HostBlock {
     std::vector<cd> P;   // tri(L) x n x n
     std::vector<cd> RC;  // L x n x eta
     // device
-    DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dSh, dPerm, dGoff, dM64, dM32, dD, dMlist, dP64, dP32, dRC64,
-        dRC32, dCols;
+    DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dOmegaHatFF, dSh, dPerm, dGoff, dM64, dM32, dD32, dD64, dMlist,
+        dP64, dP32, dRC64, dRC32, dCols;
     DBuf dCot, dEbar, dTbar, dSbar, dSumT, dSumS, dSumE;
     void release() {
-        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dSh, &dPerm, &dGoff, &dM64, &dM32, &dD, &dMlist, &dP64, &dP32, &dRC64,
+        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dOmegaHatFF, &dSh, &dPerm, &dGoff, &dM64, &dM32, &dD32, &dD64, &dMlist, &dP64, &dP32, &dRC64,
                         &dRC32, &dCols, &dCot, &dEbar, &dTbar, &dSbar, &dSumT, &dSumS, &dSumE})
             b->release();
     }
@@ -147,6 +158,7 @@ struct ef_circuit {
     std::vector<int> shared_gates;
     std::vector<cd> WS;  // 2^k_sh weights of the shared gates
     std::vector<float2> WS32;
+    std::vector<float4> WSFF;  // WS as float pairs
     bool exact_ok = true;
     std::string exact_why;
     bool approx_ok = true;
@@ -160,7 +172,7 @@ struct ef_circuit {
     double R0 = 1.0;
 
     bool dirty = true;
-    DBuf dWS, dWS32, dList, dListCount, dRecomp, dBits, dOut, dErr, dGradP, dGrad, dPbar, dSumP;
+    DBuf dWS, dWS32, dWSFF, dList, dListCount, dRecomp, dBits, dOut, dErr, dGradP, dGrad, dPbar, dSumP;
     DBuf daT, daq, dalayer, damodes, daPart, dCounters;
     cudaStream_t own_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -175,7 +187,7 @@ struct ef_circuit {
 
     ~ef_circuit() {
         for (int b = 0; b < ef::kMaxBlocks; ++b) blk[b].release();
-        for (DBuf* d : {&dWS, &dWS32, &dList, &dListCount, &dRecomp, &dBits, &dOut, &dErr, &dGradP, &dGrad, &dPbar, &dSumP, &daT,
+        for (DBuf* d : {&dWS, &dWS32, &dWSFF, &dList, &dListCount, &dRecomp, &dBits, &dOut, &dErr, &dGradP, &dGrad, &dPbar, &dSumP, &daT,
                         &daq, &dalayer, &damodes, &daPart, &dCounters})
             d->release();
         if (ev0) cudaEventDestroy(ev0);
@@ -464,6 +476,7 @@ int prepare(ef_circuit* c) {
         B.Omega.clear();
         B.Omega32.clear();
         B.OmegaHat.clear();
+        B.OmegaHatFF.clear();
         B.sh.clear();
         B.perm.clear();
         B.goff.clear();
@@ -499,6 +512,7 @@ int prepare(ef_circuit* c) {
                         B.OmegaHat[i | h] = a - b2;
                     }
             for (cd& v : B.OmegaHat) v = std::ldexp(1.0, -B.r_loc) * v;
+            B.OmegaHatFF = to_ff(B.OmegaHat);
             const int ksh_b = c->nblocks == 2 ? k_sh : 0;
             B.sh.assign((size_t)1 << ksh_b, 0u);
             for (uint32_t xs = 0; xs < (1u << ksh_b); ++xs) {
@@ -575,6 +589,7 @@ int prepare(ef_circuit* c) {
         c->WS32.resize(c->WS.size());
         for (size_t x = 0; x < c->WS.size(); ++x)
             c->WS32[x] = make_float2((float)c->WS[x].real(), (float)c->WS[x].imag());
+        c->WSFF = to_ff(c->WS);
     }
     c->p_floor = 1e-6 * std::exp(-log_sector);
     // approx gate tables
@@ -615,6 +630,7 @@ int upload_tables(ef_circuit* c, cudaStream_t s) {
         EF_CK(upload(B.dOmega, to_d2(B.Omega), s));
         EF_CK(upload(B.dOmega32, B.Omega32, s));
         EF_CK(upload(B.dOmegaHat, to_d2(B.OmegaHat), s));
+        EF_CK(upload(B.dOmegaHatFF, B.OmegaHatFF, s));
         EF_CK(upload(B.dSh, B.sh, s));
         EF_CK(upload(B.dPerm, B.perm, s));
         EF_CK(upload(B.dGoff, B.goff, s));
@@ -629,6 +645,7 @@ int upload_tables(ef_circuit* c, cudaStream_t s) {
     }
     EF_CK(upload(c->dWS, to_d2(c->WS), s));
     EF_CK(upload(c->dWS32, c->WS32, s));
+    EF_CK(upload(c->dWSFF, c->WSFF, s));
     std::vector<uint32_t> T4(((c->aT.size() + 3) & ~(size_t)3), 0u);
     std::copy(c->aT.begin(), c->aT.end(), T4.begin());
     EF_CK(upload(c->daT, T4, s));
@@ -697,11 +714,13 @@ struct ExactBuffers {
     const double2* Omega[ef::kMaxBlocks];
     const float2* Omega32[ef::kMaxBlocks];
     const double2* OmegaHat[ef::kMaxBlocks];
+    const float4* OmegaHatFF[ef::kMaxBlocks];
     const uint32_t* sh[ef::kMaxBlocks];
     const uint32_t* perm[ef::kMaxBlocks];
     const uint32_t* goff[ef::kMaxBlocks];
     const double2* WS;
     const float2* WS32;
+    const float4* WSFF;
     int* list;   // bitstrings flagged by the FP32 pass
     int* list2;  // bitstrings still above tol after their listed determinants were redone
     int* count;  // [0] list size, [1] list2 size, [2 + B] listed determinants of block B
@@ -723,11 +742,18 @@ bool per_minor_recompute(const ef_circuit* c) {
     return minors <= 8192;
 }
 
+// Bytes per (pattern, bitstring) determinant: FP32 results (float4) unless
+// FP64-only, FP64 ones (double2) for FP64 and for the recomputes of AUTO.
+size_t det_bytes(const ef_circuit* c) {
+    const int p = c->opt.precision;
+    return (p != EF_PREC_FP64 ? sizeof(float4) : 0) + (p != EF_PREC_FP32_MINOR ? sizeof(double2) : 0);
+}
+
 // Bitstrings per batch so that the per-(pattern, bitstring) determinants stay
 // within `budget` bytes.
 int64_t exact_batch(const ef_circuit* c, int64_t nb, size_t budget) {
     size_t per = 0;
-    const size_t each = sizeof(ef::d4) + (per_minor_recompute(c) ? sizeof(int2) : 0);
+    const size_t each = det_bytes(c) + (per_minor_recompute(c) ? sizeof(int2) : 0);
     for (int b = 0; b < c->nblocks; ++b) per += ((size_t)1 << c->blk[b].r) * each;
     if (per == 0 || nb == 0) return std::max<int64_t>(nb, 1);
     return std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)(budget / per)));
@@ -773,7 +799,9 @@ ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
         cm.eta[b] = c->blk[b].eta;
         cm.r[b] = c->blk[b].r;
         cm.r_loc[b] = c->blk[b].r_loc;
-        cm.D[b] = eb.blk[b].D;
+        cm.D32[b] = eb.blk[b].D32;
+        cm.D64[b] = eb.blk[b].D64;
+        cm.OmegaHatDF[b] = eb.OmegaHatFF[b];
         cm.Omega[b] = eb.Omega[b];
         cm.Omega32[b] = eb.Omega32[b];
         cm.OmegaHat[b] = eb.OmegaHat[b];
@@ -783,6 +811,8 @@ ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
     }
     cm.WS = eb.WS;
     cm.WS32 = eb.WS32;
+    cm.WSDF = eb.WSFF;
+    cm.src = c->opt.precision == EF_PREC_FP64 ? 1 : 0;
     cm.wht = combine_by_transforms(c) ? 1 : 0;
     cm.minors = 0;
     for (int b = 0; b < c->nblocks; ++b) cm.minors += (int64_t)1 << c->blk[b].r;
@@ -860,6 +890,7 @@ int exact_enqueue_combine(ef_circuit* c, const ExactBuffers& eb, ef::ExactCombin
         for (int b = 0; b < c->nblocks; ++b)
             EF_CK(ef::launch_exact_lu_f64_minors(eb.blk[b], bits, eb.mlist[b], eb.count + 2 + b, nbb, s, st));
         ef::ExactCombineDev chk = cm;
+        chk.src = 2;
         chk.col_by_index = 1;
         chk.count_bits = 1;
         chk.count_minors = 1;
@@ -868,6 +899,7 @@ int exact_enqueue_combine(ef_circuit* c, const ExactBuffers& eb, ef::ExactCombin
         for (int b = 0; b < c->nblocks; ++b)
             EF_CK(ef::launch_exact_lu_f64(eb.blk[b], bits, nbb, eb.list2, eb.count + 1, nbb, s, st));
         cm.err_coef = 0.0;
+        cm.src = 1;
         cm.count_full = 1;
         EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, eb.list2, eb.count + 1, out, err, nullptr, nullptr, s,
                                        st));
@@ -875,6 +907,7 @@ int exact_enqueue_combine(ef_circuit* c, const ExactBuffers& eb, ef::ExactCombin
         for (int b = 0; b < c->nblocks; ++b)
             EF_CK(ef::launch_exact_lu_f64(eb.blk[b], bits, nbb, eb.list, eb.count, nbb, s, st));
         cm.err_coef = 0.0;
+        cm.src = 1;
         cm.count_bits = 1;
         cm.count_full = 1;
         EF_CK(ef::launch_exact_combine(cm, bits, nbb, nbb, eb.list, eb.count, out, err, nullptr, nullptr, s, st));
@@ -924,7 +957,9 @@ int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
         const size_t ne = (size_t)B.n * B.eta;
         EF_CK(B.dM64.ensure(ny * ne * sizeof(double2)));
         if (!fp64_only) EF_CK(B.dM32.ensure(ny * ne * sizeof(float2)));
-        EF_CK(B.dD.ensure(ny * (size_t)cap * sizeof(ef::d4)));
+        const bool d32 = c->opt.precision != EF_PREC_FP64, d64 = c->opt.precision != EF_PREC_FP32_MINOR;
+        if (d32) EF_CK(B.dD32.ensure(ny * (size_t)cap * sizeof(float4)));
+        if (d64) EF_CK(B.dD64.ensure(ny * (size_t)cap * sizeof(double2)));
         ef::ExactBlockDev& d = eb.blk[b];
         exact_block_geometry(c, b, cap, d);
         d.S0C = B.dS0C.as<double2>();
@@ -932,16 +967,19 @@ int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
         d.F = B.dF.as<uint32_t>();
         d.M64 = B.dM64.as<double2>();
         d.M32 = fp64_only ? nullptr : B.dM32.as<float2>();
-        d.D = B.dD.as<ef::d4>();
+        d.D32 = d32 ? B.dD32.as<float4>() : nullptr;
+        d.D64 = d64 ? B.dD64.as<double2>() : nullptr;
         eb.Omega[b] = B.dOmega.as<double2>();
         eb.Omega32[b] = B.dOmega32.as<float2>();
         eb.OmegaHat[b] = B.dOmegaHat.as<double2>();
+        eb.OmegaHatFF[b] = B.dOmegaHatFF.as<float4>();
         eb.sh[b] = B.dSh.as<uint32_t>();
         eb.perm[b] = B.dPerm.as<uint32_t>();
         eb.goff[b] = B.dGoff.as<uint32_t>();
     }
     eb.WS = c->dWS.as<double2>();
     eb.WS32 = c->dWS32.as<float2>();
+    eb.WSFF = c->dWSFF.as<float4>();
     EF_CK(c->dList.ensure(2 * (size_t)cap * sizeof(int)));
     EF_CK(c->dListCount.ensure(4 * sizeof(int)));
     EF_CK(c->dRecomp.ensure(2 * sizeof(unsigned long long)));
@@ -1128,7 +1166,7 @@ int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_
     for (int b = 0; b < c->nblocks; ++b) {
         const HostBlock& B = c->blk[b];
         const size_t ny = (size_t)1 << B.r;
-        need += ny * (size_t)nb * (sizeof(ef::d4) + sizeof(double2)) + (size_t)nb * ((size_t)1 << B.r_loc) * 16 +
+        need += ny * (size_t)nb * (2 * sizeof(double2)) + (size_t)nb * ((size_t)1 << B.r_loc) * 16 +
                 ny * ((size_t)B.L * B.n * B.n + (size_t)B.n * B.eta) * 16;
     }
     need += (size_t)nb * ((size_t)1 << ksh) * 16;
@@ -1147,7 +1185,7 @@ int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_
         const size_t ny = (size_t)1 << B.r;
         const size_t ne = (size_t)B.n * B.eta;
         EF_CK(B.dM64.ensure(ny * ne * sizeof(double2)));
-        EF_CK(B.dD.ensure(ny * (size_t)nb * sizeof(ef::d4)));
+        EF_CK(B.dD64.ensure(ny * (size_t)nb * sizeof(double2)));
         EF_CK(B.dCot.ensure(ny * (size_t)nb * sizeof(double2)));
         EF_CK(B.dEbar.ensure((size_t)nb * ((size_t)1 << B.r_loc) * sizeof(double2)));
         EF_CK(B.dTbar.ensure(ny * std::max<size_t>(1, (size_t)B.L * B.n * B.n) * sizeof(double2)));
@@ -1162,13 +1200,15 @@ int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_
         d.F = B.dF.as<uint32_t>();
         d.M64 = B.dM64.as<double2>();
         d.M32 = nullptr;
-        d.D = B.dD.as<ef::d4>();
+        d.D32 = nullptr;
+        d.D64 = B.dD64.as<double2>();
         cm.mask[b][0] = B.mask[0];
         cm.mask[b][1] = B.mask[1];
         cm.eta[b] = B.eta;
         cm.r[b] = B.r;
         cm.r_loc[b] = B.r_loc;
-        cm.D[b] = d.D;
+        cm.D64[b] = d.D64;
+        cm.src = 1;
         cm.Omega[b] = B.dOmega.as<double2>();
         cm.s[b] = B.dSh.as<uint32_t>();
         cm.perm[b] = B.dPerm.as<uint32_t>();
@@ -1641,15 +1681,18 @@ size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* bas
         eb.Omega[b] = cv.take<double2>(B.Omega.size());
         eb.Omega32[b] = cv.take<float2>(B.Omega32.size());
         eb.OmegaHat[b] = cv.take<double2>(B.OmegaHat.size());
+        eb.OmegaHatFF[b] = cv.take<float4>(B.OmegaHat.size());
         eb.sh[b] = cv.take<uint32_t>(B.sh.size());
         eb.perm[b] = cv.take<uint32_t>(B.perm.size());
         eb.goff[b] = cv.take<uint32_t>(B.goff.size());
         d.M64 = cv.take<double2>(ny * ne);
         d.M32 = want32 ? cv.take<float2>(ny * ne) : nullptr;
-        d.D = cv.take<ef::d4>(ny * (size_t)eb.cap);
+        d.D32 = c->opt.precision != EF_PREC_FP64 ? cv.take<float4>(ny * (size_t)eb.cap) : nullptr;
+        d.D64 = c->opt.precision != EF_PREC_FP32_MINOR ? cv.take<double2>(ny * (size_t)eb.cap) : nullptr;
     }
     eb.WS = cv.take<double2>(c->WS.size());
     eb.WS32 = cv.take<float2>(c->WS32.size());
+    eb.WSFF = cv.take<float4>(c->WS.size());
     eb.list = cv.take<int>((size_t)eb.cap);
     eb.list2 = cv.take<int>((size_t)eb.cap);
     eb.count = cv.take<int>(4);
@@ -1721,6 +1764,7 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
         EF_CK(copy_in_c(eb.Omega[b], B.Omega.data(), B.Omega.size(), s));
         EF_CK(copy_in(eb.Omega32[b], B.Omega32, s));
         EF_CK(copy_in_c(eb.OmegaHat[b], B.OmegaHat.data(), B.OmegaHat.size(), s));
+        EF_CK(copy_in(eb.OmegaHatFF[b], B.OmegaHatFF, s));
         EF_CK(copy_in(eb.sh[b], B.sh, s));
         EF_CK(copy_in(eb.perm[b], B.perm, s));
         EF_CK(copy_in(eb.goff[b], B.goff, s));
@@ -1730,6 +1774,7 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
     }
     EF_CK(copy_in_c(eb.WS, c->WS.data(), c->WS.size(), s));
     EF_CK(copy_in(eb.WS32, c->WS32, s));
+    EF_CK(copy_in(eb.WSFF, c->WSFF, s));
     return run_exact(c, eb, d_bits, nb, d_out, d_err_out, s, st);
 }
 

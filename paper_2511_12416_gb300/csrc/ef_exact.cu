@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
         if (b >= nb) continue;
         for (int t = 0; t < Y; ++t) {
             const size_t z = (size_t)chunk * Y + t;
-            d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
+            float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
             if (ok) {
                 const float2* Mt = smM + (size_t)t * n * S;
                 float2 A[ETA][ETA];
@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
                 }
                 float er2, zabs2;
                 const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
-                res = make_d4((double)det.x, (double)det.y, (double)er2, (double)zabs2);
+                res = make_float4(det.x, det.y, er2, zabs2);
             }
-            B.D[z * nb + b] = res;
+            B.D32[z * nb + b] = res;
         }
     }
 }
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restri
             const bool ok = decode_rows<ETA>(E.bits[2 * b], E.bits[2 * b + 1], B.mask0, B.mask1, rows);
             for (int t = 0; t < Y; ++t) {
                 const size_t z = (size_t)chunk * Y + t;
-                d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
+                float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (ok) {
                     const float2* Mt = smQ + (size_t)t * n * S;
                     float2 A[ETA][ETA];
@@ -230,9 +230,9 @@ __global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restri
                     }
                     float er2, zabs2;
                     const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
-                    res = make_d4((double)det.x, (double)det.y, (double)er2, (double)zabs2);
+                    res = make_float4(det.x, det.y, er2, zabs2);
                 }
-                B.D[z * E.nb + b] = res;
+                B.D32[z * E.nb + b] = res;
             }
         }
         __syncthreads();
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const ui
         const int64_t pos = item - z * count;
         const int64_t b = list ? (int64_t)list[pos] : pos;
         int rows[ETA];
-        d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
+        double2 res = make_double2(0.0, 0.0);
         if (decode_rows<ETA>(bits[2 * b], bits[2 * b + 1], B.mask0, B.mask1, rows)) {
             const double2* Mz = B.M64 + (size_t)z * n * ETA;
             double2 A[ETA][ETA];
@@ -304,15 +304,14 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const ui
             for (int i = 0; i < ETA; ++i)
 #pragma unroll
                 for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
-            const double2 det = lu_det_plain<double, ETA>(A);
-            res = make_d4(det.x, det.y, 0.0, 0.0);
+            res = lu_det_plain<double, ETA>(A);
         }
-        B.D[(size_t)z * stride + pos] = res;
+        B.D64[(size_t)z * stride + pos] = res;
     }
 }
 
 // Thread <-> one listed determinant (bitstring column, pattern z): redone in
-// FP64 in place, with zero error terms.
+// FP64 into D64, and marked in D32 (er2 = -1).
 template <int ETA>
 __global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B, const uint64_t* __restrict__ bits,
                                                        const int2* __restrict__ mlist,
@@ -325,7 +324,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B, const ui
         const int64_t pos = e.x;
         const int z = e.y;
         int rows[ETA];
-        d4 res = make_d4(0.0, 0.0, 0.0, 0.0);
+        double2 res = make_double2(0.0, 0.0);
         if (decode_rows<ETA>(bits[2 * pos], bits[2 * pos + 1], B.mask0, B.mask1, rows)) {
             const double2* Mz = B.M64 + (size_t)z * n * ETA;
             double2 A[ETA][ETA];
@@ -333,10 +332,10 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B, const ui
             for (int i = 0; i < ETA; ++i)
 #pragma unroll
                 for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
-            const double2 det = lu_det_plain<double, ETA>(A);
-            res = make_d4(det.x, det.y, 0.0, 0.0);
+            res = lu_det_plain<double, ETA>(A);
         }
-        B.D[(size_t)z * stride + pos] = res;
+        B.D64[(size_t)z * stride + pos] = res;
+        B.D32[(size_t)z * stride + pos] = make_float4(0.f, 0.f, -1.f, 0.f);
     }
 }
 
@@ -416,9 +415,13 @@ __global__ void __launch_bounds__(256) k_exact_lu_rows(ExactBlockDev B, const ui
             for (int j = 0; j < G; ++j) rowv[j] = (live && j < eta) ? src[j] : mk(R(0), R(0));
             R er2, zabs2;
             const T det = lu_det_rows<R, G>(rowv, r, eta, er2, zabs2);
-            if (valid && r == 0)
-                B.D[z * stride + pos] = ok ? make_d4((double)det.x, (double)det.y, (double)er2, (double)zabs2)
-                                           : make_d4(0.0, 0.0, 0.0, 0.0);
+            if (valid && r == 0) {
+                if constexpr (std::is_same<R, double>::value)
+                    B.D64[z * stride + pos] = ok ? det : make_double2(0.0, 0.0);
+                else
+                    B.D32[z * stride + pos] = ok ? make_float4(det.x, det.y, er2, zabs2)
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
     }
 }
@@ -496,6 +499,85 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// ---- float-pair ("double-float") arithmetic for the transform path over FP32
+// determinants: a value is hi + lo with |lo| <= ulp(hi)/2, about 48 bits.
+// Sums use the error-free two-sum (Knuth) and products the FMA residual
+// (Dekker's product with a fused multiply-add), each renormalised.
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 quick_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
+    const float2 s = two_sum(x.x, y.x);
+    return quick_two_sum(s.x, s.y + (x.y + y.y));
+}
+__device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 ff_mul(float2 x, float2 y) {
+    const float p = x.x * y.x;
+    const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));
+    return quick_two_sum(p, e);
+}
+// complex float pairs as float4 (re hi, re lo, im hi, im lo)
+__device__ __forceinline__ float4 cf_add(float4 a, float4 b) {
+    const float2 r = ff_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    const float2 i = ff_add(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    return make_float4(r.x, r.y, i.x, i.y);
+}
+__device__ __forceinline__ float4 cf_sub(float4 a, float4 b) {
+    const float2 r = ff_add(make_float2(a.x, a.y), ff_neg(make_float2(b.x, b.y)));
+    const float2 i = ff_add(make_float2(a.z, a.w), ff_neg(make_float2(b.z, b.w)));
+    return make_float4(r.x, r.y, i.x, i.y);
+}
+__device__ __forceinline__ float4 cf_mul(float4 a, float4 b) {
+    const float2 ar = make_float2(a.x, a.y), ai = make_float2(a.z, a.w);
+    const float2 br = make_float2(b.x, b.y), bi = make_float2(b.z, b.w);
+    const float2 r = ff_add(ff_mul(ar, br), ff_neg(ff_mul(ai, bi)));
+    const float2 i = ff_add(ff_mul(ar, bi), ff_mul(ai, br));
+    return make_float4(r.x, r.y, i.x, i.y);
+}
+
+// Walsh-Hadamard stage over bit j on float pairs, optionally followed by the
+// product with W[index & lm].
+__device__ __forceinline__ void wht_stage_ff(float4* F, int half, int j, const float4* W, uint32_t lm, int tid,
+                                             int nt) {
+    for (int q = tid; q < half; q += nt) {
+        const int i0 = ((q >> j) << (j + 1)) | (q & ((1 << j) - 1));
+        const int i1 = i0 | (1 << j);
+        const float4 a = F[i0], b = F[i1];
+        float4 u = cf_add(a, b);
+        float4 v = cf_sub(a, b);
+        if (W) {
+            u = cf_mul(u, W[i0 & lm]);
+            v = cf_mul(v, W[i1 & lm]);
+        }
+        F[i0] = u;
+        F[i1] = v;
+    }
+}
+
+// Determinant z of block B for D column col, as the combine's source says.
+__device__ __forceinline__ double2 det_at(const ExactCombineDev& C, int B, size_t idx) {
+    if (C.src == 1) return C.D64[B][idx];
+    const float4 v = C.D32[B][idx];
+    if (C.src == 2 && v.z < 0.f) return C.D64[B][idx];
+    return make_double2((double)v.x, (double)v.y);
+}
+// |det|^2 er2 + zabs2 of an FP32 determinant (0 for one redone in FP64); an
+// infinite or undefined term (0 x inf after a vanishing pivot) is taken as the
+// largest float, an error too large to bound
+__device__ __forceinline__ float err_term(const ExactCombineDev& C, int B, size_t idx) {
+    const float4 v = C.D32[B][idx];
+    if (v.z < 0.f) return 0.f;
+    const float t = fmaf(fmaf(v.x, v.x, v.y * v.y), v.z, v.w);
+    return t <= 3.0e38f ? t : 3.0e38f;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -528,17 +610,20 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                                                        int* __restrict__ append_count) {
     constexpr int NT = 256;
     constexpr int NW = NT / 32;
-    // dynamic shared memory: [F_0 (2^r_0), F_1 (2^r_1) double2 when C.wht]
-    // [FP32 copies of A_0, A_1 (2^k_sh each) for the error estimate]
-    // [the variance term of every determinant (2^r_0 + 2^r_1 floats) when
-    //  listing the determinants to redo in FP64]
+    // dynamic shared memory: [F_0 (2^r_0), F_1 (2^r_1), 16 bytes each, when C.wht:
+    // double2, or float pairs over FP32 determinants] [FP32 copies of A_0, A_1
+    // (2^k_sh each) for the error estimate] [the variance term of every
+    // determinant (2^r_0 + 2^r_1 floats) when listing the ones to redo in FP64]
     extern __shared__ double2 smDyn[];
     __shared__ double red[3 * NW];
     __shared__ double s_theta;
     const int nsh = 1 << C.k_sh;
     const int nF = C.wht ? (1 << C.r[0]) + (1 << C.r[1]) : 0;
+    const bool ffw = C.wht && C.src == 0;  // transforms on float pairs
     double2* F0 = smDyn;
     double2* F1 = smDyn + (C.wht ? (1 << C.r[0]) : 0);
+    float4* G0 = reinterpret_cast<float4*>(F0);
+    float4* G1 = reinterpret_cast<float4*>(F1);
     float2* smA32 = reinterpret_cast<float2*>(smDyn + nF);
     float* smV = reinterpret_cast<float*>(smA32 + 2 * nsh);
     const int tid = threadIdx.x;
@@ -566,31 +651,64 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
             }
             continue;
         }
-        double ar = 0.0, ai = 0.0, var = 0.0;
+        double ar = 0.0, ai = 0.0;
+        float var = 0.f;
         if (C.nblocks == 0) {
             ar = tid == 0 ? 1.0 : 0.0;
         } else if (C.nblocks == 1) {
             // amp = sum_z Omega(z) det(z); C(z) = Omega(z)
             const int nz = 1 << C.r[0];
             for (int z = tid; z < nz; z += NT) {
-                const d4 v = C.D[0][(size_t)z * stride + col];
+                const size_t idx = (size_t)z * stride + col;
+                const double2 v = det_at(C, 0, idx);
                 const double2 w = C.Omega[0][z];
                 ar = fma(w.x, v.x, fma(-w.y, v.y, ar));
                 ai = fma(w.x, v.y, fma(w.y, v.x, ai));
                 if (want_err) {
-                    const double vt = (w.x * w.x + w.y * w.y) * fma(v.x * v.x + v.y * v.y, v.z, v.w);
+                    const float2 w32 = C.Omega32[0][z];
+                    const float vt = fmaf(w32.x, w32.x, w32.y * w32.y) * err_term(C, 0, idx);
                     var += vt;
-                    if (emit) smV[z] = (float)vt;
+                    if (emit) smV[z] = vt;
                 }
             }
+        } else if (ffw) {
+            // FP32 determinants: transforms and products on float pairs
+            for (int B = 0; B < 2; ++B) {
+                float4* GB = B ? G1 : G0;
+                const int nz = 1 << C.r[B];
+                for (int z = tid; z < nz; z += NT) {
+                    const float4 v = C.D32[B][(size_t)z * stride + col];
+                    GB[z] = make_float4(v.x, 0.f, v.y, 0.f);
+                }
+            }
+            __syncthreads();
+            const int rl = max(C.r_loc[0], C.r_loc[1]);
+            for (int pass = 0; pass < 2; ++pass)
+                for (int j = 0; j < rl; ++j) {
+                    for (int B = 0; B < 2; ++B) {
+                        if (j >= C.r_loc[B]) continue;
+                        const bool mul = pass == 0 && j == C.r_loc[B] - 1;
+                        wht_stage_ff(B ? G1 : G0, 1 << (C.r[B] - 1), j, mul ? C.OmegaHatDF[B] : nullptr,
+                                     (1u << C.r_loc[B]) - 1u, tid, NT);
+                    }
+                    __syncthreads();
+                }
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int xs = tid; xs < nsh; xs += NT) {
+                const float4 a0 = G0[C.s[0][xs]], a1 = G1[C.s[1][xs]];
+                if (want_err) {
+                    smA32[xs] = make_float2(a0.x, a0.z);
+                    smA32[nsh + xs] = make_float2(a1.x, a1.z);
+                }
+                acc = cf_add(acc, cf_mul(C.WSDF[xs], cf_mul(a0, a1)));
+            }
+            ar = (double)acc.x + (double)acc.y;
+            ai = (double)acc.z + (double)acc.w;
         } else if (C.wht) {
             for (int B = 0; B < 2; ++B) {
                 double2* FB = B ? F1 : F0;
                 const int nz = 1 << C.r[B];
-                for (int z = tid; z < nz; z += NT) {
-                    const d4 v = C.D[B][(size_t)z * stride + col];
-                    FB[z] = make_double2(v.x, v.y);
-                }
+                for (int z = tid; z < nz; z += NT) FB[z] = det_at(C, B, (size_t)z * stride + col);
             }
             __syncthreads();
             // forward transform (the last stage also multiplies by the transformed
@@ -625,7 +743,7 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                     const int nl = B == 0 ? nl0 : nl1;
                     double sx = 0.0, sy = 0.0;
                     for (int zl = 0; zl < nl; ++zl) {
-                        const d4 v = C.D[B][(size_t)(zl ^ sB) * stride + col];
+                        const double2 v = det_at(C, B, (size_t)(zl ^ sB) * stride + col);
                         const double2 w = C.Omega[B][zl];
                         sx = fma(w.x, v.x, fma(-w.y, v.y, sx));
                         sy = fma(w.x, v.y, fma(w.y, v.x, sy));
@@ -656,7 +774,7 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
         }
         const double p = ar * ar + ai * ai;
         if (want_err && C.nblocks == 2) {
-            // the estimate needs no FP64: coefficients in FP32
+            // the estimate needs no FP64: coefficients and terms in FP32
             for (int B = 0; B < 2; ++B) {
                 const int nz = 1 << C.r[B];
                 const uint32_t lmask = (1u << C.r_loc[B]) - 1u;
@@ -671,24 +789,23 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                         cx += t.x;
                         cy += t.y;
                     }
-                    const d4 v = C.D[B][(size_t)z * stride + col];
-                    const double c2 = (double)cx * cx + (double)cy * cy;
-                    const double vt = c2 * fma(v.x * v.x + v.y * v.y, v.z, v.w);
+                    const float vt = fmaf(cx, cx, cy * cy) * err_term(C, B, (size_t)z * stride + col);
                     var += vt;
-                    if (emit) smV[B * voff1 + z] = (float)vt;
+                    if (emit) smV[B * voff1 + z] = vt;
                 }
             }
         }
-        var = warp_sum(var);
-        if ((tid & 31) == 0) red[2 * NW + (tid >> 5)] = var;
+        double dvar = warp_sum((double)var);
+        if ((tid & 31) == 0) red[2 * NW + (tid >> 5)] = dvar;
         __syncthreads();
         if (tid == 0) {
-            var = red[2 * NW];
+            dvar = red[2 * NW];
 #pragma unroll
-            for (int w = 1; w < NW; ++w) var += red[2 * NW + w];
+            for (int w = 1; w < NW; ++w) dvar += red[2 * NW + w];
+            // |p~ - p| <= 2 |amp| s + s^2 for an amplitude error of size s
             const double sp = sqrt(p);
-            const double dabs = 2.0 * sp * C.err_coef * sqrt(var);
-            const double e = dabs / fmax(p, C.p_floor);
+            const double sig = C.err_coef * sqrt(dvar);
+            const double e = fma(2.0 * sp, sig, sig * sig) / fmax(p, C.p_floor);
             out[b] = p;
             if (list) {
                 if (err) err[b] = -fabs(err[b]);
@@ -701,10 +818,12 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                 append_list[idx] = (int)b;
             }
             if (emit) {
-                // variance at which the estimate equals tol; determinants whose term
-                // exceeds half of it shared over all of them are redone, so the
-                // terms left cannot sum past half of it
-                const double vt = C.tol * fmax(p, C.p_floor) / (2.0 * sp * C.err_coef);
+                // variance at which the estimate equals tol (s_t: root of
+                // 2 sp s + s^2 = tol max(p, floor)); determinants whose term exceeds
+                // half of it shared over all of them are redone, so the terms left
+                // cannot sum past half of it
+                const double st = C.tol * fmax(p, C.p_floor) / (sp + sqrt(fma(C.tol, fmax(p, C.p_floor), p)));
+                const double vt = st / C.err_coef;
                 s_theta = flag ? 0.5 * vt * vt / (double)C.minors : -1.0;
             }
         }

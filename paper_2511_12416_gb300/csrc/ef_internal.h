@@ -7,13 +7,6 @@
 
 namespace ef {
 
-// One partial branch sum of the Exact path: (re, im) of sum_y w(y) det, and
-// S = sum_y |w|^2 |det|^2, E = sum_y |w|^2 e_det^2 for the FP32 error estimate
-struct __align__(32) d4 {
-    double x, y, z, w;
-};
-__host__ __device__ inline d4 make_d4(double x, double y, double z, double w) { return d4{x, y, z, w}; }
-
 constexpr int kMaxModes = 128;
 constexpr int kMaxBlocks = 2;      // independent mode blocks kept factorised
 constexpr int kMaxEtaRows = 32;    // warp-row LU: one lane per minor row
@@ -46,7 +39,9 @@ struct ExactBlockDev {
     const uint32_t* F;      // L x n: flip masks over pattern bits
     double2* M64;           // 2^r x n x eta branch matrices (FP64)
     float2* M32;            // same, FP32 (may be null)
-    d4* D;                  // [2^r][stride]: (det re, det im, er2, zabs2) per (pattern, bitstring)
+    // determinants per (pattern, bitstring column), [2^r][stride] each:
+    float4* D32;            // FP32 LU: (det re, det im, er2, zabs2); er2 < 0 marks one redone in D64
+    double2* D64;           // FP64 LU: det
 };
 
 // amp(b) = sum_{x_sh} WS[x_sh] prod_B A_B(x_sh),
@@ -58,7 +53,9 @@ struct ExactCombineDev {
     uint64_t mask[kMaxBlocks][2];
     int eta[kMaxBlocks];
     int r[kMaxBlocks], r_loc[kMaxBlocks];
-    const d4* D[kMaxBlocks];
+    const float4* D32[kMaxBlocks];
+    const double2* D64[kMaxBlocks];
+    int src;                           // determinants from D32 (0), D64 (1), D32 with D64 where marked (2)
     const double2* Omega[kMaxBlocks];  // 2^r_loc pattern weights of the local gates
     const uint32_t* s[kMaxBlocks];     // 2^k_sh: pattern of the shared bits
     const uint32_t* perm[kMaxBlocks];  // shared bit patterns x_sh grouped by s >> r_loc
@@ -66,6 +63,8 @@ struct ExactCombineDev {
     const double2* WS;                 // 2^k_sh weights of the shared gates
     const float2* Omega32[kMaxBlocks]; // FP32 copies for the error estimate
     const double2* OmegaHat[kMaxBlocks];  // 2^r_loc: Walsh-Hadamard transform of Omega times 2^-r_loc
+    const float4* OmegaHatDF[kMaxBlocks]; // the same as float pairs (re hi, re lo, im hi, im lo)
+    const float4* WSDF;                   // WS as float pairs
     int wht;                           // 1: XOR convolutions by transforms in shared memory
     const float2* WS32;
     double err_coef;                   // K u32 (FP32 path), 0 for FP64

@@ -36,10 +36,10 @@ CASES = [
 
 
 @pytest.mark.parametrize("name,maker", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("auto", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5), ("auto", 1e-5)])
 def test_noalloc_matches_allocating_entry_point_twice(lib, name, maker, prec, tol):
     c, bits = maker()
-    precision = lib.EF_PREC_FP64 if prec == "fp64" else lib.EF_PREC_AUTO
+    precision = {"fp64": lib.EF_PREC_FP64, "fp32": lib.EF_PREC_FP32_MINOR, "auto": lib.EF_PREC_AUTO}[prec]
     nb = len(bits)
     d_bits = torch.from_numpy(np.ascontiguousarray(bits).view(np.int64)).cuda()
     ref = torch.empty(nb, dtype=torch.float64, device="cuda")
