@@ -120,17 +120,18 @@ struct HostBlock {
     std::vector<float4> OmegaHatFF;  // the same as float pairs
     std::vector<uint32_t> sh;      // 2^k_sh: pattern of each shared bit vector
     std::vector<uint32_t> perm, goff;  // shared bit vectors grouped by pattern >> r_loc
+    std::vector<uint32_t> inv_off, inv_xs;  // shared bit vectors grouped by pattern
     std::vector<uint32_t> coord;       // pattern coordinates of the local, then shared gates
     int c_log2 = 0;
     // Raw Estimate
     std::vector<cd> P;   // tri(L) x n x n
     std::vector<cd> RC;  // L x n x eta
     // device
-    DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dOmegaHatFF, dSh, dPerm, dGoff, dM64, dM32, dD32, dD64, dMlist,
+    DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dOmegaHatFF, dSh, dPerm, dGoff, dInvOff, dInvXs, dM64, dM32, dD32, dD64, dMlist,
         dP64, dP32, dRC64, dRC32, dCols;
     DBuf dCot, dEbar, dTbar, dSbar, dSumT, dSumS, dSumE;
     void release() {
-        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dOmegaHatFF, &dSh, &dPerm, &dGoff, &dM64, &dM32, &dD32, &dD64, &dMlist, &dP64, &dP32, &dRC64,
+        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dOmegaHatFF, &dSh, &dPerm, &dGoff, &dInvOff, &dInvXs, &dM64, &dM32, &dD32, &dD64, &dMlist, &dP64, &dP32, &dRC64,
                         &dRC32, &dCols, &dCot, &dEbar, &dTbar, &dSbar, &dSumT, &dSumS, &dSumE})
             b->release();
     }
@@ -480,6 +481,8 @@ int prepare(ef_circuit* c) {
         B.sh.clear();
         B.perm.clear();
         B.goff.clear();
+        B.inv_off.clear();
+        B.inv_xs.clear();
         if (c->exact_ok) {
             // Omega(z) = sum of w_loc(y) over the local bit vectors y with pattern z
             static const cd ipow[4] = {cd(1, 0), cd(0, 1), cd(-1, 0), cd(0, -1)};
@@ -528,6 +531,12 @@ int prepare(ef_circuit* c) {
             B.perm.assign(B.sh.size(), 0u);
             std::vector<uint32_t> fill(B.goff.begin(), B.goff.end() - 1);
             for (uint32_t xs = 0; xs < B.sh.size(); ++xs) B.perm[fill[B.sh[xs] >> B.r_loc]++] = xs;
+            B.inv_off.assign(((size_t)1 << B.r) + 1, 0u);
+            for (uint32_t xs = 0; xs < B.sh.size(); ++xs) B.inv_off[B.sh[xs] + 1]++;
+            for (size_t z = 0; z + 1 < B.inv_off.size(); ++z) B.inv_off[z + 1] += B.inv_off[z];
+            B.inv_xs.assign(B.sh.size(), 0u);
+            std::vector<uint32_t> fz(B.inv_off.begin(), B.inv_off.end() - 1);
+            for (uint32_t xs = 0; xs < B.sh.size(); ++xs) B.inv_xs[fz[B.sh[xs]]++] = xs;
         }
 
         // ---- Raw Estimate: interval products and right factors
@@ -634,6 +643,8 @@ int upload_tables(ef_circuit* c, cudaStream_t s) {
         EF_CK(upload(B.dSh, B.sh, s));
         EF_CK(upload(B.dPerm, B.perm, s));
         EF_CK(upload(B.dGoff, B.goff, s));
+        EF_CK(upload(B.dInvOff, B.inv_off, s));
+        EF_CK(upload(B.dInvXs, B.inv_xs, s));
         std::vector<float2> P32(B.P.size()), RC32(B.RC.size());
         for (size_t e = 0; e < B.P.size(); ++e) P32[e] = make_float2((float)B.P[e].real(), (float)B.P[e].imag());
         for (size_t e = 0; e < B.RC.size(); ++e) RC32[e] = make_float2((float)B.RC[e].real(), (float)B.RC[e].imag());
@@ -718,6 +729,8 @@ struct ExactBuffers {
     const uint32_t* sh[ef::kMaxBlocks];
     const uint32_t* perm[ef::kMaxBlocks];
     const uint32_t* goff[ef::kMaxBlocks];
+    const uint32_t* inv_off[ef::kMaxBlocks];
+    const uint32_t* inv_xs[ef::kMaxBlocks];
     const double2* WS;
     const float2* WS32;
     const float4* WSFF;
@@ -808,12 +821,20 @@ ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
         cm.s[b] = eb.sh[b];
         cm.perm[b] = eb.perm[b];
         cm.goff[b] = eb.goff[b];
+        cm.inv_off[b] = eb.inv_off[b];
+        cm.inv_xs[b] = eb.inv_xs[b];
     }
     cm.WS = eb.WS;
     cm.WS32 = eb.WS32;
     cm.WSDF = eb.WSFF;
     cm.src = c->opt.precision == EF_PREC_FP64 ? 1 : 0;
     cm.wht = combine_by_transforms(c) ? 1 : 0;
+    cm.wreg = 0;
+    if (cm.wht && c->opt.precision != EF_PREC_FP64) {
+        cm.wreg = 1;
+        for (int b = 0; b < 2; ++b)
+            if (c->blk[b].r < 5 || c->blk[b].r > 10 || c->blk[b].r_loc > 5) cm.wreg = 0;
+    }
     cm.minors = 0;
     for (int b = 0; b < c->nblocks; ++b) cm.minors += (int64_t)1 << c->blk[b].r;
     cm.mcount = eb.count + 2;
@@ -976,6 +997,8 @@ int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
         eb.sh[b] = B.dSh.as<uint32_t>();
         eb.perm[b] = B.dPerm.as<uint32_t>();
         eb.goff[b] = B.dGoff.as<uint32_t>();
+        eb.inv_off[b] = B.dInvOff.as<uint32_t>();
+        eb.inv_xs[b] = B.dInvXs.as<uint32_t>();
     }
     eb.WS = c->dWS.as<double2>();
     eb.WS32 = c->dWS32.as<float2>();
@@ -1685,6 +1708,8 @@ size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* bas
         eb.sh[b] = cv.take<uint32_t>(B.sh.size());
         eb.perm[b] = cv.take<uint32_t>(B.perm.size());
         eb.goff[b] = cv.take<uint32_t>(B.goff.size());
+        eb.inv_off[b] = cv.take<uint32_t>(B.inv_off.size());
+        eb.inv_xs[b] = cv.take<uint32_t>(B.inv_xs.size());
         d.M64 = cv.take<double2>(ny * ne);
         d.M32 = want32 ? cv.take<float2>(ny * ne) : nullptr;
         d.D32 = c->opt.precision != EF_PREC_FP64 ? cv.take<float4>(ny * (size_t)eb.cap) : nullptr;
@@ -1768,6 +1793,8 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
         EF_CK(copy_in(eb.sh[b], B.sh, s));
         EF_CK(copy_in(eb.perm[b], B.perm, s));
         EF_CK(copy_in(eb.goff[b], B.goff, s));
+        EF_CK(copy_in(eb.inv_off[b], B.inv_off, s));
+        EF_CK(copy_in(eb.inv_xs[b], B.inv_xs, s));
         k_gather_columns<<<32, 128, 0, s>>>(tb.S0[b], tb.cols[b], B.n, B.eta, const_cast<double2*>(d.S0C));
         EF_CK(cudaGetLastError());
         st.launches += 1;

@@ -571,11 +571,47 @@ __device__ __forceinline__ double2 det_at(const ExactCombineDev& C, int B, size_
 // |det|^2 er2 + zabs2 of an FP32 determinant (0 for one redone in FP64); an
 // infinite or undefined term (0 x inf after a vanishing pivot) is taken as the
 // largest float, an error too large to bound
-__device__ __forceinline__ float err_term(const ExactCombineDev& C, int B, size_t idx) {
-    const float4 v = C.D32[B][idx];
+__device__ __forceinline__ float err_term_v(float4 v) {
     if (v.z < 0.f) return 0.f;
     const float t = fmaf(fmaf(v.x, v.x, v.y * v.y), v.z, v.w);
     return t <= 3.0e38f ? t : 3.0e38f;
+}
+__device__ __forceinline__ float err_term(const ExactCombineDev& C, int B, size_t idx) {
+    return err_term_v(C.D32[B][idx]);
+}
+
+// Butterfly over lane bit j of a value held one per lane: the lane whose
+// element index has bit j clear gets v + partner, the other partner - v.
+__device__ __forceinline__ float4 lane_butterfly(float4 v, int j, bool upper) {
+    float4 o;
+    o.x = __shfl_xor_sync(0xffffffffu, v.x, 1 << j);
+    o.y = __shfl_xor_sync(0xffffffffu, v.y, 1 << j);
+    o.z = __shfl_xor_sync(0xffffffffu, v.z, 1 << j);
+    o.w = __shfl_xor_sync(0xffffffffu, v.w, 1 << j);
+    return cf_add(o, upper ? make_float4(-v.x, -v.y, -v.z, -v.w) : v);
+}
+__device__ __forceinline__ float2 lane_butterfly(float2 v, int j, bool upper) {
+    const float ox = __shfl_xor_sync(0xffffffffu, v.x, 1 << j);
+    const float oy = __shfl_xor_sync(0xffffffffu, v.y, 1 << j);
+    return upper ? make_float2(ox - v.x, oy - v.y) : make_float2(v.x + ox, v.y + oy);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ float4 warp_sum_cf(float4 v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        float4 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v.x, off);
+        o.y = __shfl_xor_sync(0xffffffffu, v.y, off);
+        o.z = __shfl_xor_sync(0xffffffffu, v.z, off);
+        o.w = __shfl_xor_sync(0xffffffffu, v.w, off);
+        v = cf_add(v, o);
+    }
+    return v;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -603,7 +639,7 @@ __device__ __forceinline__ void wht_stage(double2* F, int half, int j, const dou
     }
 }
 
-__global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const uint64_t* __restrict__ bits,
+__global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, const uint64_t* __restrict__ bits,
                                                        int64_t nb, int64_t stride, const int* __restrict__ list,
                                                        const int* __restrict__ list_count, double* __restrict__ out,
                                                        double* __restrict__ err, int* __restrict__ append_list,
@@ -615,7 +651,9 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
     // (2^k_sh each) for the error estimate] [the variance term of every
     // determinant (2^r_0 + 2^r_1 floats) when listing the ones to redo in FP64]
     extern __shared__ double2 smDyn[];
-    __shared__ double red[3 * NW];
+    __shared__ double red[2 * NW];
+    __shared__ float4 redf[NW];
+    __shared__ float redv[NW];
     __shared__ double s_theta;
     const int nsh = 1 << C.k_sh;
     const int nF = C.wht ? (1 << C.r[0]) + (1 << C.r[1]) : 0;
@@ -652,6 +690,7 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
             continue;
         }
         double ar = 0.0, ai = 0.0;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);  // float-pair amplitude of the transform path
         float var = 0.f;
         if (C.nblocks == 0) {
             ar = tid == 0 ? 1.0 : 0.0;
@@ -693,7 +732,6 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                     }
                     __syncthreads();
                 }
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int xs = tid; xs < nsh; xs += NT) {
                 const float4 a0 = G0[C.s[0][xs]], a1 = G1[C.s[1][xs]];
                 if (want_err) {
@@ -702,8 +740,6 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                 }
                 acc = cf_add(acc, cf_mul(C.WSDF[xs], cf_mul(a0, a1)));
             }
-            ar = (double)acc.x + (double)acc.y;
-            ai = (double)acc.z + (double)acc.w;
         } else if (C.wht) {
             for (int B = 0; B < 2; ++B) {
                 double2* FB = B ? F1 : F0;
@@ -756,24 +792,21 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                 ai += t.y;
             }
         }
-        // amplitude: warp butterflies, then the warps' partial sums in a fixed
-        // order (every thread forms the same total)
-        ar = warp_sum(ar);
-        ai = warp_sum(ai);
-        if ((tid & 31) == 0) {
-            red[tid >> 5] = ar;
-            red[NW + (tid >> 5)] = ai;
+        // amplitude: warp butterflies, then thread 0 adds the warps' partial sums
+        // in a fixed order
+        if (ffw) {
+            acc = warp_sum_cf(acc);
+            if ((tid & 31) == 0) redf[tid >> 5] = acc;
+        } else {
+            ar = warp_sum(ar);
+            ai = warp_sum(ai);
+            if ((tid & 31) == 0) {
+                red[tid >> 5] = ar;
+                red[NW + (tid >> 5)] = ai;
+            }
         }
-        __syncthreads();
-        ar = red[0];
-        ai = red[NW];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) {
-            ar += red[w];
-            ai += red[NW + w];
-        }
-        const double p = ar * ar + ai * ai;
         if (want_err && C.nblocks == 2) {
+            __syncthreads();  // smA32 complete
             // the estimate needs no FP64: coefficients and terms in FP32
             for (int B = 0; B < 2; ++B) {
                 const int nz = 1 << C.r[B];
@@ -795,13 +828,26 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
                 }
             }
         }
-        double dvar = warp_sum((double)var);
-        if ((tid & 31) == 0) red[2 * NW + (tid >> 5)] = dvar;
+        var = warp_sum_f(var);
+        if ((tid & 31) == 0) redv[tid >> 5] = var;
         __syncthreads();
         if (tid == 0) {
-            dvar = red[2 * NW];
-#pragma unroll
-            for (int w = 1; w < NW; ++w) dvar += red[2 * NW + w];
+            if (ffw) {
+                acc = redf[0];
+                for (int w = 1; w < NW; ++w) acc = cf_add(acc, redf[w]);
+                ar = (double)acc.x + (double)acc.y;
+                ai = (double)acc.z + (double)acc.w;
+            } else {
+                ar = red[0];
+                ai = red[NW];
+                for (int w = 1; w < NW; ++w) {
+                    ar += red[w];
+                    ai += red[NW + w];
+                }
+            }
+            const double p = ar * ar + ai * ai;
+            double dvar = 0.0;
+            for (int w = 0; w < NW; ++w) dvar += (double)redv[w];
             // |p~ - p| <= 2 |amp| s + s^2 for an amplitude error of size s
             const double sp = sqrt(p);
             const double sig = C.err_coef * sqrt(dvar);
@@ -844,6 +890,174 @@ __global__ void __launch_bounds__(256) k_exact_combine(ExactCombineDev C, const 
     }
 }
 
+// Primary pass over FP32 determinants when both blocks have 32 <= 2^r <= 1024
+// patterns and at most 5 local pattern bits (ExactCombineDev.wreg). Same
+// arithmetic as k_exact_combine's float-pair path, organised for throughput:
+//  * thread <-> elements e = tid + NT i of each block, so the local pattern
+//    bits are lane bits and both transforms (float pairs for the amplitude,
+//    FP32 for the error coefficients) run in registers by shuffles;
+//  * the error coefficients are XOR convolutions too: C_B(h, .) = Omega_B
+//    convolved with Q_B(h, .), Q_B(z) = sum of w_sh A_other over the x_sh with
+//    s_B(x_sh) = z;
+//  * shared memory is double-buffered by iteration parity and each
+//    bitstring's totals, flag and determinant list are finished by one warp
+//    (rotating), so no CTA-wide barrier waits for that serial tail.
+template <int NT>
+__global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, const uint64_t* __restrict__ bits,
+                                                             int64_t nb, int64_t stride, double* __restrict__ out,
+                                                             double* __restrict__ err, int* __restrict__ append_list,
+                                                             int* __restrict__ append_count) {
+    constexpr int NW = NT / 32;
+    extern __shared__ float4 smF[];
+    __shared__ float4 redf[2][NW];
+    __shared__ float redv[2][NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsh = 1 << C.k_sh;
+    const int n0 = 1 << C.r[0], n1 = 1 << C.r[1];
+    const bool want_err = C.err_coef > 0.0;
+    const bool emit = want_err && C.mlist[0] != nullptr;
+    // per buffer: G_0 (n0), G_1 (n1) float4; A_0, A_1 (nsh each) float2; V (n0 + n1) float
+    const size_t buf_words = (size_t)4 * (n0 + n1) + (size_t)4 * nsh + (emit ? (size_t)(n0 + n1) : 0);
+    int it = 0;
+    for (int64_t pos = blockIdx.x; pos < nb; pos += gridDim.x, ++it) {
+        const int buf = it & 1;
+        float* base = reinterpret_cast<float*>(smF) + (size_t)buf * buf_words;
+        float4* G0 = reinterpret_cast<float4*>(base);
+        float4* G1 = G0 + n0;
+        float2* A32 = reinterpret_cast<float2*>(G1 + n1);
+        float* V = reinterpret_cast<float*>(A32 + 2 * nsh);
+        const int tail = it % NW;  // warp that finishes this bitstring
+        const uint64_t w0 = bits[2 * pos], w1 = bits[2 * pos + 1];
+        bool ok = ((w0 & C.inactive0) == 0) && ((w1 & C.inactive1) == 0);
+        for (int B = 0; B < 2; ++B)
+            ok = ok && (__popcll(w0 & C.mask[B][0]) + __popcll(w1 & C.mask[B][1]) == C.eta[B]);
+        if (!ok) {
+            if (tid == 0) {
+                out[pos] = 0.0;
+                if (err) err[pos] = 0.0;
+            }
+            continue;
+        }
+        float errt[2][kWregMax];
+        // 1. F_B = Omega_B convolved with det_B over the local bits (float pairs)
+#pragma unroll
+        for (int B = 0; B < 2; ++B) {
+            const int nz = B ? n1 : n0;
+            const int rl = C.r_loc[B];
+            const uint32_t lm = (1u << rl) - 1u;
+            float4* GB = B ? G1 : G0;
+#pragma unroll
+            for (int i = 0; i < kWregMax; ++i) {
+                const int e = tid + NT * i;
+                if (e >= nz) break;
+                const float4 d = C.D32[B][(size_t)e * stride + pos];
+                errt[B][i] = want_err ? err_term_v(d) : 0.f;
+                float4 v = make_float4(d.x, 0.f, d.y, 0.f);
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int j = 0; j < rl; ++j) {
+                        v = lane_butterfly(v, j, (e >> j) & 1);
+                        if (pass == 0 && j == rl - 1) v = cf_mul(v, C.OmegaHatDF[B][e & lm]);
+                    }
+                GB[e] = v;
+            }
+        }
+        __syncthreads();
+        // 2. amp = sum_xs WS(xs) F_0(s_0(xs)) F_1(s_1(xs))
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int xs = tid; xs < nsh; xs += NT) {
+            const float4 a0 = G0[C.s[0][xs]], a1 = G1[C.s[1][xs]];
+            A32[xs] = make_float2(a0.x, a0.z);
+            A32[nsh + xs] = make_float2(a1.x, a1.z);
+            acc = cf_add(acc, cf_mul(C.WSDF[xs], cf_mul(a0, a1)));
+        }
+        float var = 0.f;
+        if (want_err) {
+            __syncthreads();  // A32 complete
+#pragma unroll
+            for (int B = 0; B < 2; ++B) {
+                const int nz = B ? n1 : n0;
+                const int rl = C.r_loc[B];
+                const uint32_t lm = (1u << rl) - 1u;
+                const float2* Aoth = A32 + (1 - B) * nsh;
+#pragma unroll
+                for (int i = 0; i < kWregMax; ++i) {
+                    const int e = tid + NT * i;
+                    if (e >= nz) break;
+                    float2 q = make_float2(0.f, 0.f);
+                    for (uint32_t g = C.inv_off[B][e]; g < C.inv_off[B][e + 1]; ++g) {
+                        const uint32_t xs = C.inv_xs[B][g];
+                        const float2 t = cmul(C.WS32[xs], Aoth[xs]);
+                        q.x += t.x;
+                        q.y += t.y;
+                    }
+                    for (int pass = 0; pass < 2; ++pass)
+                        for (int j = 0; j < rl; ++j) {
+                            q = lane_butterfly(q, j, (e >> j) & 1);
+                            if (pass == 0 && j == rl - 1) {
+                                const float4 w = C.OmegaHatDF[B][e & lm];
+                                q = cmul(q, make_float2(w.x, w.z));
+                            }
+                        }
+                    const float vt = fmaf(q.x, q.x, q.y * q.y) * errt[B][i];
+                    var += vt;
+                    if (emit) V[B * n0 + e] = vt;
+                }
+            }
+        }
+        acc = warp_sum_cf(acc);
+        var = warp_sum_f(var);
+        if (lane == 0) {
+            redf[buf][warp] = acc;
+            redv[buf][warp] = var;
+        }
+        __syncthreads();
+        if (warp != tail) continue;
+        // 3. the tail warp: totals in a fixed order (lanes 0..NW-1 then butterflies)
+        float4 a = lane < NW ? redf[buf][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float vv = lane < NW ? redv[buf][lane] : 0.f;
+#pragma unroll
+        for (int off = NW / 2; off > 0; off >>= 1) {
+            float4 o;
+            o.x = __shfl_xor_sync(0xffffffffu, a.x, off);
+            o.y = __shfl_xor_sync(0xffffffffu, a.y, off);
+            o.z = __shfl_xor_sync(0xffffffffu, a.z, off);
+            o.w = __shfl_xor_sync(0xffffffffu, a.w, off);
+            a = cf_add(a, o);
+            vv += __shfl_xor_sync(0xffffffffu, vv, off);
+        }
+        float theta = -1.f;
+        if (lane == 0) {
+            const double ar = (double)a.x + (double)a.y, ai = (double)a.z + (double)a.w;
+            const double p = ar * ar + ai * ai;
+            out[pos] = p;
+            // error estimate in FP32: |p~ - p| <= 2 |amp| s + s^2 for an amplitude error s
+            const float pf = (float)p, floor = (float)C.p_floor, tol = (float)C.tol, ec = (float)C.err_coef;
+            const float pm = fmaxf(pf, floor);
+            const float sp = sqrtf(pf);
+            const float sig = ec * sqrtf(vv);
+            const float e = fmaf(2.f * sp, sig, sig * sig) / pm;
+            if (err) err[pos] = (double)e;
+            if (append_list && !(e <= tol)) {
+                append_list[atomicAdd(append_count, 1)] = (int)pos;
+                if (emit) {
+                    // variance at which the estimate equals tol; terms above half of
+                    // it shared over all determinants are redone in FP64
+                    const float st = tol * pm / (sp + sqrtf(fmaf(tol, pm, pf)));
+                    const float vt = st / ec;
+                    theta = 0.5f * vt * vt / (float)C.minors;
+                }
+            }
+        }
+        theta = __shfl_sync(0xffffffffu, theta, 0);
+        if (theta >= 0.f)
+            for (int B = 0; B < 2; ++B) {
+                const int nz = B ? n1 : n0;
+                for (int z = lane; z < nz; z += 32)
+                    if (V[B * n0 + z] > theta) C.mlist[B][atomicAdd(&C.mcount[B], 1)] = make_int2((int)pos, z);
+            }
+    }
+}
+
 size_t exact_combine_smem(const ExactCombineDev& c) {
     size_t smem = (size_t)2 * ((size_t)1 << c.k_sh) * sizeof(float2);
     if (c.wht) smem += (((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1])) * sizeof(double2);
@@ -855,6 +1069,21 @@ cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits,
                                  const int* list, const int* list_count, double* out, double* err, int* append_list,
                                  int* append_count, cudaStream_t s, LaunchStats& st) {
     if (nb <= 0) return cudaSuccess;
+    if (c.wreg && c.src == 0 && !list && !c.col_by_index) {
+        constexpr int NT = 256;
+        const size_t words = (size_t)4 * (((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1])) +
+                             (size_t)4 * ((size_t)1 << c.k_sh) +
+                             (c.mlist[0] ? ((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1]) : 0);
+        const size_t smem = 2 * words * sizeof(float);
+        cudaError_t e = cudaFuncSetAttribute(k_exact_combine_ffr<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, 152 * 12));
+        k_exact_combine_ffr<NT><<<(unsigned)blocks, NT, smem, s>>>(c, bits, nb, stride, out, err, append_list,
+                                                                   append_count);
+        st.launches += 1;
+        return cudaGetLastError();
+    }
     const size_t smem = exact_combine_smem(c);
     cudaError_t e = cudaFuncSetAttribute(k_exact_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -18,6 +18,7 @@ constexpr int kMaxApproxStored = 64;  // rank-one columns kept per trajectory
 constexpr int kMaxExactPatternBits = 22;  // 2^22 flip patterns per block
 constexpr int kMaxExactLocalBits = 22;    // local gates per block
 constexpr int kMaxExactSharedBits = 12;   // gates shared by the two blocks
+constexpr int kWregMax = 4;               // elements per thread and block of the combine's register path
 
 // ---------------------------------------------------------------- Exact mode
 
@@ -66,6 +67,10 @@ struct ExactCombineDev {
     const float4* OmegaHatDF[kMaxBlocks]; // the same as float pairs (re hi, re lo, im hi, im lo)
     const float4* WSDF;                   // WS as float pairs
     int wht;                           // 1: XOR convolutions by transforms in shared memory
+    int wreg;                          // 1: transforms over FP32 determinants in registers
+                                       //    (5 <= r <= 10 and 1 <= r_loc <= 5 in both blocks)
+    const uint32_t* inv_off[kMaxBlocks];  // 2^r + 1: x_sh with s_B(x_sh) = z are
+    const uint32_t* inv_xs[kMaxBlocks];   //   inv_xs[inv_off[z] .. inv_off[z + 1])
     const float2* WS32;
     double err_coef;                   // K u32 (FP32 path), 0 for FP64
     double tol, p_floor;
