@@ -904,8 +904,10 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
 //    (rotating), so no CTA-wide barrier waits for that serial tail.
 template <int NT>
 __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, const uint64_t* __restrict__ bits,
-                                                             int64_t nb, int64_t stride, double* __restrict__ out,
-                                                             double* __restrict__ err, int* __restrict__ append_list,
+                                                             int64_t nb, int64_t stride, const int* __restrict__ list,
+                                                             const int* __restrict__ list_count,
+                                                             double* __restrict__ out, double* __restrict__ err,
+                                                             int* __restrict__ append_list,
                                                              int* __restrict__ append_count) {
     constexpr int NW = NT / 32;
     extern __shared__ float4 smF[];
@@ -914,12 +916,20 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nsh = 1 << C.k_sh;
     const int n0 = 1 << C.r[0], n1 = 1 << C.r[1];
+    const int64_t count = list ? (int64_t)(*list_count) : nb;
+    if (C.recomp && blockIdx.x == 0 && tid == 0) {
+        if (C.count_bits) atomicAdd(&C.recomp[0], (unsigned long long)count);
+        if (C.count_minors)
+            for (int B = 0; B < 2; ++B) atomicAdd(&C.recomp[1], (unsigned long long)C.mcount[B]);
+    }
     const bool want_err = C.err_coef > 0.0;
-    const bool emit = want_err && C.mlist[0] != nullptr;
+    const bool emit = want_err && !list && C.mlist[0] != nullptr;
     // per buffer: G_0 (n0), G_1 (n1) float4; A_0, A_1 (nsh each) float2; V (n0 + n1) float
     const size_t buf_words = (size_t)4 * (n0 + n1) + (size_t)4 * nsh + (emit ? (size_t)(n0 + n1) : 0);
     int it = 0;
-    for (int64_t pos = blockIdx.x; pos < nb; pos += gridDim.x, ++it) {
+    for (int64_t pos = blockIdx.x; pos < count; pos += gridDim.x, ++it) {
+        const int64_t b = list ? (int64_t)list[pos] : pos;
+        const int64_t col = C.col_by_index ? b : pos;  // column of D holding this bitstring's determinants
         const int buf = it & 1;
         float* base = reinterpret_cast<float*>(smF) + (size_t)buf * buf_words;
         float4* G0 = reinterpret_cast<float4*>(base);
@@ -927,14 +937,14 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
         float2* A32 = reinterpret_cast<float2*>(G1 + n1);
         float* V = reinterpret_cast<float*>(A32 + 2 * nsh);
         const int tail = it % NW;  // warp that finishes this bitstring
-        const uint64_t w0 = bits[2 * pos], w1 = bits[2 * pos + 1];
+        const uint64_t w0 = bits[2 * b], w1 = bits[2 * b + 1];
         bool ok = ((w0 & C.inactive0) == 0) && ((w1 & C.inactive1) == 0);
         for (int B = 0; B < 2; ++B)
             ok = ok && (__popcll(w0 & C.mask[B][0]) + __popcll(w1 & C.mask[B][1]) == C.eta[B]);
         if (!ok) {
             if (tid == 0) {
-                out[pos] = 0.0;
-                if (err) err[pos] = 0.0;
+                out[b] = 0.0;
+                if (err && !list) err[b] = 0.0;
             }
             continue;
         }
@@ -950,9 +960,15 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
             for (int i = 0; i < kWregMax; ++i) {
                 const int e = tid + NT * i;
                 if (e >= nz) break;
-                const float4 d = C.D32[B][(size_t)e * stride + pos];
+                const size_t idx = (size_t)e * stride + col;
+                const float4 d = C.D32[B][idx];
                 errt[B][i] = want_err ? err_term_v(d) : 0.f;
                 float4 v = make_float4(d.x, 0.f, d.y, 0.f);
+                if (C.src == 2 && d.z < 0.f) {  // redone in FP64: as a float pair
+                    const double2 w = C.D64[B][idx];
+                    const float xh = (float)w.x, yh = (float)w.y;
+                    v = make_float4(xh, (float)(w.x - (double)xh), yh, (float)(w.y - (double)yh));
+                }
                 for (int pass = 0; pass < 2; ++pass)
                     for (int j = 0; j < rl; ++j) {
                         v = lane_butterfly(v, j, (e >> j) & 1);
@@ -1025,36 +1041,57 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
             a = cf_add(a, o);
             vv += __shfl_xor_sync(0xffffffffu, vv, off);
         }
-        float theta = -1.f;
+        float budget = -1.f;
         if (lane == 0) {
             const double ar = (double)a.x + (double)a.y, ai = (double)a.z + (double)a.w;
             const double p = ar * ar + ai * ai;
-            out[pos] = p;
+            out[b] = p;
             // error estimate in FP32: |p~ - p| <= 2 |amp| s + s^2 for an amplitude error s
             const float pf = (float)p, floor = (float)C.p_floor, tol = (float)C.tol, ec = (float)C.err_coef;
             const float pm = fmaxf(pf, floor);
             const float sp = sqrtf(pf);
             const float sig = ec * sqrtf(vv);
-            const float e = fmaf(2.f * sp, sig, sig * sig) / pm;
-            if (err) err[pos] = (double)e;
+            const float e = want_err ? fmaf(2.f * sp, sig, sig * sig) / pm : 0.f;
+            if (list) {
+                if (err) err[b] = -fabs(err[b]);
+            } else if (err) {
+                err[b] = (double)e;
+            }
             if (append_list && !(e <= tol)) {
-                append_list[atomicAdd(append_count, 1)] = (int)pos;
+                append_list[atomicAdd(append_count, 1)] = (int)b;
                 if (emit) {
-                    // variance at which the estimate equals tol; terms above half of
-                    // it shared over all determinants are redone in FP64
+                    // half the variance at which the estimate equals tol
                     const float st = tol * pm / (sp + sqrtf(fmaf(tol, pm, pf)));
                     const float vt = st / ec;
-                    theta = 0.5f * vt * vt / (float)C.minors;
+                    budget = 0.5f * vt * vt;
                 }
             }
         }
-        theta = __shfl_sync(0xffffffffu, theta, 0);
-        if (theta >= 0.f)
+        budget = __shfl_sync(0xffffffffu, budget, 0);
+        if (budget >= 0.f) {
+            // the largest threshold t whose terms <= t sum to at most the budget
+            // (bisection on the bit patterns of non-negative floats); the
+            // determinants with larger terms are redone in FP64
+            uint32_t lo = 0u, hi = 0x7f800000u;  // [0, +inf]
+            while (hi - lo > 1u) {
+                const uint32_t mid = lo + ((hi - lo) >> 1);
+                const float t = __uint_as_float(mid);
+                float sum = 0.f;
+                for (int z = lane; z < n0 + n1; z += 32) {
+                    const float v = V[z];
+                    sum += v <= t ? v : 0.f;
+                }
+                sum = warp_sum_f(sum);
+                if (sum <= budget) lo = mid;
+                else hi = mid;
+            }
+            const float t = __uint_as_float(lo);
             for (int B = 0; B < 2; ++B) {
                 const int nz = B ? n1 : n0;
                 for (int z = lane; z < nz; z += 32)
-                    if (V[B * n0 + z] > theta) C.mlist[B][atomicAdd(&C.mcount[B], 1)] = make_int2((int)pos, z);
+                    if (!(V[B * n0 + z] <= t)) C.mlist[B][atomicAdd(&C.mcount[B], 1)] = make_int2((int)pos, z);
             }
+        }
     }
 }
 
@@ -1069,7 +1106,7 @@ cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits,
                                  const int* list, const int* list_count, double* out, double* err, int* append_list,
                                  int* append_count, cudaStream_t s, LaunchStats& st) {
     if (nb <= 0) return cudaSuccess;
-    if (c.wreg && c.src == 0 && !list && !c.col_by_index) {
+    if (c.wreg && (c.src == 0 || c.src == 2) && !c.count_full) {
         constexpr int NT = 256;
         const size_t words = (size_t)4 * (((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1])) +
                              (size_t)4 * ((size_t)1 << c.k_sh) +
@@ -1079,8 +1116,8 @@ cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, 152 * 12));
-        k_exact_combine_ffr<NT><<<(unsigned)blocks, NT, smem, s>>>(c, bits, nb, stride, out, err, append_list,
-                                                                   append_count);
+        k_exact_combine_ffr<NT><<<(unsigned)blocks, NT, smem, s>>>(c, bits, nb, stride, list, list_count, out, err,
+                                                                   append_list, append_count);
         st.launches += 1;
         return cudaGetLastError();
     }
