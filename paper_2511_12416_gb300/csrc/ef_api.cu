@@ -829,6 +829,10 @@ ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
     cm.WSDF = eb.WSFF;
     cm.src = c->opt.precision == EF_PREC_FP64 ? 1 : 0;
     cm.wht = combine_by_transforms(c) ? 1 : 0;
+    cm.inj = c->nblocks == 2 ? 1 : 0;
+    for (int b = 0; b < c->nblocks && cm.inj; ++b)
+        for (size_t z = 0; z + 1 < c->blk[b].inv_off.size(); ++z)
+            if (c->blk[b].inv_off[z + 1] - c->blk[b].inv_off[z] > 1) cm.inj = 0;
     cm.wreg = 0;
     if (cm.wht && c->opt.precision != EF_PREC_FP64) {
         cm.wreg = 1;

@@ -1095,6 +1095,259 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
     }
 }
 
+// In-register Walsh-Hadamard transform of NL = 2^RL values (one row of a block).
+template <int RL, typename T, typename Add, typename Sub>
+__device__ __forceinline__ void row_wht(T (&v)[1 << RL], Add add, Sub sub) {
+#pragma unroll
+    for (int j = 0; j < RL; ++j)
+#pragma unroll
+        for (int l = 0; l < (1 << RL); ++l)
+            if (!(l & (1 << j))) {
+                const T a = v[l], c = v[l | (1 << j)];
+                v[l] = add(a, c);
+                v[l | (1 << j)] = sub(a, c);
+            }
+}
+
+// Warp per bitstring: the primary and re-estimating passes over FP32
+// determinants when both blocks have RL local pattern bits. A pattern
+// z = (h, l) belongs to row (B, h); a lane owns whole rows, so the XOR
+// convolutions over l (float pairs for the amplitude, FP32 for the error
+// coefficients) run inside one thread, and a warp never waits for another.
+// The arithmetic is that of k_exact_combine's float-pair path; the warp's
+// shared memory holds F_B (float pairs), then A_B (FP32) and the variance
+// terms for the determinant list.
+template <int RL, int RPL>
+__global__ void __launch_bounds__(128) k_exact_combine_wp(ExactCombineDev C, const uint64_t* __restrict__ bits,
+                                                          int64_t nb, int64_t stride, const int* __restrict__ list,
+                                                          const int* __restrict__ list_count,
+                                                          double* __restrict__ out, double* __restrict__ err,
+                                                          int* __restrict__ append_list,
+                                                          int* __restrict__ append_count) {
+    constexpr int NL = 1 << RL;  // RPL: rows per lane at most
+    extern __shared__ float4 smWp[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int n0 = 1 << C.r[0], n1 = 1 << C.r[1];
+    const int rows0 = n0 >> RL, rows = rows0 + (n1 >> RL);
+    const int nsh = 1 << C.k_sh;
+    const int64_t count = list ? (int64_t)(*list_count) : nb;
+    if (C.recomp && blockIdx.x == 0 && threadIdx.x == 0) {
+        if (C.count_bits) atomicAdd(&C.recomp[0], (unsigned long long)count);
+        if (C.count_minors)
+            for (int B = 0; B < 2; ++B) atomicAdd(&C.recomp[1], (unsigned long long)C.mcount[B]);
+    }
+    const bool want_err = C.err_coef > 0.0;
+    const bool emit = want_err && !list && C.mlist[0] != nullptr;
+    // per warp: G_0, G_1 (n0 + n1 float4; after step 2 reused for V, n0 + n1
+    // float) | A_0, A_1 (2 nsh float2) or, when every s_B is one-to-one (C.inj),
+    // Q_0, Q_1 (n0 + n1 float2) scattered in step 2
+    const size_t warp_f4 = (size_t)(n0 + n1) + (size_t)max(nsh, (n0 + n1 + 1) / 2);
+    float4* G = smWp + (size_t)wib * warp_f4;
+    float2* A32 = reinterpret_cast<float2*>(G + n0 + n1);
+    float2* Q = A32;
+    float* V = reinterpret_cast<float*>(G);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t pos = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; pos < count; pos += nwarps) {
+        const int64_t b = list ? (int64_t)list[pos] : pos;
+        const int64_t col = C.col_by_index ? b : pos;
+        const uint64_t w0 = bits[2 * b], w1 = bits[2 * b + 1];
+        bool ok = ((w0 & C.inactive0) == 0) && ((w1 & C.inactive1) == 0);
+        for (int B = 0; B < 2; ++B)
+            ok = ok && (__popcll(w0 & C.mask[B][0]) + __popcll(w1 & C.mask[B][1]) == C.eta[B]);
+        if (!ok) {
+            if (lane == 0) {
+                out[b] = 0.0;
+                if (err && !list) err[b] = 0.0;
+            }
+            continue;
+        }
+        float errt[RPL][NL];
+        // 1. rows of F_B = Omega_B convolved with det_B over l, in float pairs
+#pragma unroll
+        for (int rr = 0; rr < RPL; ++rr) {
+            const int row = lane + 32 * rr;
+            if (row >= rows) break;
+            const int B = row < rows0 ? 0 : 1;
+            const int z0 = (B ? row - rows0 : row) << RL;
+            float4 v[NL];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                const size_t idx = (size_t)(z0 | l) * stride + col;
+                const float4 d = C.D32[B][idx];
+                errt[rr][l] = want_err ? err_term_v(d) : 0.f;
+                v[l] = make_float4(d.x, 0.f, d.y, 0.f);
+                if (C.src == 2 && d.z < 0.f) {  // redone in FP64: as a float pair
+                    const double2 w = C.D64[B][idx];
+                    const float xh = (float)w.x, yh = (float)w.y;
+                    v[l] = make_float4(xh, (float)(w.x - (double)xh), yh, (float)(w.y - (double)yh));
+                }
+            }
+            row_wht<RL>(v, cf_add, cf_sub);
+            const float4* Wh = C.OmegaHatDF[B];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) v[l] = cf_mul(v[l], Wh[l]);
+            row_wht<RL>(v, cf_add, cf_sub);
+            float4* GB = G + (B ? n0 : 0) + z0;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) GB[l] = v[l];
+        }
+        __syncwarp();
+        // 2. amp = sum_xs WS(xs) F_0(s_0(xs)) F_1(s_1(xs)); with one-to-one s_B,
+        //    also Q_B(s_B(xs)) = w_sh(xs) A_other(xs) (FP32)
+        const bool scatter = want_err && C.inj;
+        if (scatter) {
+            for (int z = lane; z < n0 + n1; z += 32) Q[z] = make_float2(0.f, 0.f);
+            __syncwarp();
+        }
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int xs = lane; xs < nsh; xs += 32) {
+            const uint32_t z0 = C.s[0][xs], z1 = C.s[1][xs];
+            const float4 a0 = G[z0], a1 = G[n0 + z1];
+            const float4 w = C.WSDF[xs];
+            if (scatter) {
+                const float2 w32 = make_float2(w.x, w.z);
+                Q[z0] = cmul(w32, make_float2(a1.x, a1.z));
+                Q[n0 + z1] = cmul(w32, make_float2(a0.x, a0.z));
+            } else if (want_err) {
+                A32[xs] = make_float2(a0.x, a0.z);
+                A32[nsh + xs] = make_float2(a1.x, a1.z);
+            }
+            acc = cf_add(acc, cf_mul(w, cf_mul(a0, a1)));
+        }
+        float var = 0.f;
+        if (want_err) {
+            __syncwarp();
+            // 3. rows of C_B = Omega_B convolved with Q_B, Q_B(z) = sum of w_sh A_other
+            //    over the x_sh with s_B(x_sh) = z (FP32)
+#pragma unroll
+            for (int rr = 0; rr < RPL; ++rr) {
+                const int row = lane + 32 * rr;
+                if (row >= rows) break;
+                const int B = row < rows0 ? 0 : 1;
+                const int z0 = (B ? row - rows0 : row) << RL;
+                const float2* Aoth = A32 + (1 - B) * nsh;
+                float2 q[NL];
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    q[l] = make_float2(0.f, 0.f);
+                    if (scatter) {
+                        q[l] = Q[(B ? n0 : 0) + (z0 | l)];
+                        continue;
+                    }
+                    for (uint32_t g = C.inv_off[B][z0 | l]; g < C.inv_off[B][(z0 | l) + 1]; ++g) {
+                        const uint32_t xs = C.inv_xs[B][g];
+                        const float2 t = cmul(C.WS32[xs], Aoth[xs]);
+                        q[l].x += t.x;
+                        q[l].y += t.y;
+                    }
+                }
+                const auto fadd = [](float2 a, float2 c) { return make_float2(a.x + c.x, a.y + c.y); };
+                const auto fsub = [](float2 a, float2 c) { return make_float2(a.x - c.x, a.y - c.y); };
+                row_wht<RL>(q, fadd, fsub);
+                const float4* Wh = C.OmegaHatDF[B];
+#pragma unroll
+                for (int l = 0; l < NL; ++l) q[l] = cmul(q[l], make_float2(Wh[l].x, Wh[l].z));
+                row_wht<RL>(q, fadd, fsub);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    const float vt = fmaf(q[l].x, q[l].x, q[l].y * q[l].y) * errt[rr][l];
+                    var += vt;
+                    if (emit) V[(B ? n0 : 0) + (z0 | l)] = vt;
+                }
+            }
+        }
+        // 4. totals (fixed butterfly order), estimate, flag, determinant list
+        acc = warp_sum_cf(acc);
+        var = warp_sum_f(var);
+        float budget = -1.f;
+        if (lane == 0) {
+            const double ar = (double)acc.x + (double)acc.y, ai = (double)acc.z + (double)acc.w;
+            const double p = ar * ar + ai * ai;
+            out[b] = p;
+            // |p~ - p| <= 2 |amp| s + s^2 for an amplitude error s (in FP32)
+            const float pf = (float)p, tol = (float)C.tol, ec = (float)C.err_coef;
+            const float pm = fmaxf(pf, (float)C.p_floor);
+            const float sp = sqrtf(pf);
+            const float sig = ec * sqrtf(var);
+            const float e = want_err ? fmaf(2.f * sp, sig, sig * sig) / pm : 0.f;
+            if (list) {
+                if (err) err[b] = -fabs(err[b]);
+            } else if (err) {
+                err[b] = (double)e;
+            }
+            if (append_list && !(e <= tol)) {
+                append_list[atomicAdd(append_count, 1)] = (int)b;
+                if (emit) {
+                    const float st = tol * pm / (sp + sqrtf(fmaf(tol, pm, pf)));
+                    const float vt = st / ec;
+                    budget = 0.5f * vt * vt;  // half the variance at which the estimate equals tol
+                }
+            }
+        }
+        budget = __shfl_sync(0xffffffffu, budget, 0);
+        if (budget >= 0.f) {
+            __syncwarp();
+            // the largest threshold whose terms sum to at most the budget, by
+            // bisection on float bit patterns; larger terms are redone in FP64
+            uint32_t lo = 0u, hi = 0x7f800000u;
+            while (hi - lo > 1u) {
+                const uint32_t mid = lo + ((hi - lo) >> 1);
+                const float t = __uint_as_float(mid);
+                float sum = 0.f;
+                for (int z = lane; z < n0 + n1; z += 32) {
+                    const float x = V[z];
+                    sum += x <= t ? x : 0.f;
+                }
+                if (warp_sum_f(sum) <= budget) lo = mid;
+                else hi = mid;
+            }
+            const float t = __uint_as_float(lo);
+            for (int z = lane; z < n0 + n1; z += 32)
+                if (!(V[z] <= t)) {
+                    const int B = z < n0 ? 0 : 1;
+                    C.mlist[B][atomicAdd(&C.mcount[B], 1)] = make_int2((int)pos, B ? z - n0 : z);
+                }
+        }
+        __syncwarp();
+    }
+}
+
+// Shared memory per warp of k_exact_combine_wp (bytes), 0 if it does not apply.
+size_t exact_combine_wp_bytes(const ExactCombineDev& c) {
+    if (c.nblocks != 2 || c.r_loc[0] != c.r_loc[1] || c.r_loc[0] < 1 || c.r_loc[0] > 5) return 0;
+    const int rows = (1 << (c.r[0] - c.r_loc[0])) + (1 << (c.r[1] - c.r_loc[1]));
+    if (rows > 64) return 0;
+    const size_t n = ((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1]);
+    // matches the kernel's per-warp layout
+    const size_t bytes = 16 * (n + std::max(((size_t)1 << c.k_sh), (n + 1) / 2));
+    return bytes <= 24 * 1024 ? bytes : 0;
+}
+
+template <int RL, int RPL>
+static cudaError_t launch_wp_r(const ExactCombineDev& c, size_t per_warp, const uint64_t* bits, int64_t nb,
+                               int64_t stride, const int* list, const int* list_count, double* out, double* err,
+                               int* append_list, int* append_count, cudaStream_t s) {
+    const size_t smem = 4 * per_warp;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_exact_combine_wp<RL, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nb + 3) / 4, 152 * 8));
+    k_exact_combine_wp<RL, RPL><<<(unsigned)blocks, 128, smem, s>>>(c, bits, nb, stride, list, list_count, out, err,
+                                                                    append_list, append_count);
+    return cudaGetLastError();
+}
+
+template <int RL>
+static cudaError_t launch_wp(const ExactCombineDev& c, size_t per_warp, const uint64_t* bits, int64_t nb,
+                             int64_t stride, const int* list, const int* list_count, double* out, double* err,
+                             int* append_list, int* append_count, cudaStream_t s) {
+    const int rows = (1 << (c.r[0] - RL)) + (1 << (c.r[1] - RL));
+    return rows <= 32 ? launch_wp_r<RL, 1>(c, per_warp, bits, nb, stride, list, list_count, out, err, append_list,
+                                           append_count, s)
+                      : launch_wp_r<RL, 2>(c, per_warp, bits, nb, stride, list, list_count, out, err, append_list,
+                                           append_count, s);
+}
+
 size_t exact_combine_smem(const ExactCombineDev& c) {
     size_t smem = (size_t)2 * ((size_t)1 << c.k_sh) * sizeof(float2);
     if (c.wht) smem += (((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1])) * sizeof(double2);
@@ -1106,6 +1359,19 @@ cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits,
                                  const int* list, const int* list_count, double* out, double* err, int* append_list,
                                  int* append_count, cudaStream_t s, LaunchStats& st) {
     if (nb <= 0) return cudaSuccess;
+    const size_t wp = (c.src == 0 || c.src == 2) && !c.count_full ? exact_combine_wp_bytes(c) : 0;
+    if (wp) {
+        cudaError_t e;
+        switch (c.r_loc[0]) {
+            case 1: e = launch_wp<1>(c, wp, bits, nb, stride, list, list_count, out, err, append_list, append_count, s); break;
+            case 2: e = launch_wp<2>(c, wp, bits, nb, stride, list, list_count, out, err, append_list, append_count, s); break;
+            case 3: e = launch_wp<3>(c, wp, bits, nb, stride, list, list_count, out, err, append_list, append_count, s); break;
+            case 4: e = launch_wp<4>(c, wp, bits, nb, stride, list, list_count, out, err, append_list, append_count, s); break;
+            default: e = launch_wp<5>(c, wp, bits, nb, stride, list, list_count, out, err, append_list, append_count, s); break;
+        }
+        st.launches += 1;
+        return e;
+    }
     if (c.wreg && (c.src == 0 || c.src == 2) && !c.count_full) {
         constexpr int NT = 256;
         const size_t words = (size_t)4 * (((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1])) +

@@ -69,6 +69,7 @@ struct ExactCombineDev {
     int wht;                           // 1: XOR convolutions by transforms in shared memory
     int wreg;                          // 1: transforms over FP32 determinants in registers
                                        //    (5 <= r <= 10 and 1 <= r_loc <= 5 in both blocks)
+    int inj;                           // 1: every s_B is one-to-one
     const uint32_t* inv_off[kMaxBlocks];  // 2^r + 1: x_sh with s_B(x_sh) = z are
     const uint32_t* inv_xs[kMaxBlocks];   //   inv_xs[inv_off[z] .. inv_off[z + 1])
     const float2* WS32;
