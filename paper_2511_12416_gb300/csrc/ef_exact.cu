@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const ui
 }
 
 // Thread <-> one listed determinant (bitstring column, pattern z): redone in
-// FP64 into D64, and marked in D32 (er2 = -1).
+// FP64, stored in its D64 slot as a float pair (re hi, re lo, im hi, im lo),
+// and marked in D32 (er2 = -1).
 template <int ETA>
 __global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B, const uint64_t* __restrict__ bits,
                                                        const int2* __restrict__ mlist,
@@ -334,7 +335,9 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B, const ui
                 for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
             res = lu_det_plain<double, ETA>(A);
         }
-        B.D64[(size_t)z * stride + pos] = res;
+        const float xh = (float)res.x, yh = (float)res.y;
+        reinterpret_cast<float4*>(B.D64)[(size_t)z * stride + pos] =
+            make_float4(xh, (float)(res.x - (double)xh), yh, (float)(res.y - (double)yh));
         B.D32[(size_t)z * stride + pos] = make_float4(0.f, 0.f, -1.f, 0.f);
     }
 }
@@ -561,11 +564,42 @@ __device__ __forceinline__ void wht_stage_ff(float4* F, int half, int j, const f
     }
 }
 
-// Determinant z of block B for D column col, as the combine's source says.
+// float -> double by integer operations (exact; no FP64 instruction). On this
+// GPU every FP64 instruction, even with one active lane or predicated off,
+// holds the SM sub-partition's FP64 unit for tens of cycles, so the fast
+// combines keep FP64 out of their per-bitstring code.
+__device__ __forceinline__ double f2d_int(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    const uint32_t ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+    uint64_t bits;
+    if (ex == 0xffu) {
+        bits = sign | 0x7ff0000000000000ull | ((uint64_t)man << 29);
+    } else if (ex != 0u) {
+        bits = sign | ((uint64_t)(ex + 896u) << 52) | ((uint64_t)man << 29);
+    } else if (man == 0u) {
+        bits = sign;
+    } else {  // subnormal float: normal in double
+        const int lz = __clz(man);  // leading one at bit 31 - lz
+        bits = sign | ((uint64_t)(905 - lz) << 52) | ((uint64_t)((man << (lz - 8)) & 0x7fffffu) << 29);
+    }
+    return __longlong_as_double((long long)bits);
+}
+// -|x| by setting the sign bit
+__device__ __forceinline__ double neg_abs_int(double x) {
+    return __longlong_as_double(__double_as_longlong(x) | (long long)0x8000000000000000ull);
+}
+
+// Determinant z of block B for D column col, as the combine's source says. A
+// determinant redone in FP64 for a marked FP32 entry is stored as a float
+// pair (re hi, re lo, im hi, im lo) in its D64 slot.
 __device__ __forceinline__ double2 det_at(const ExactCombineDev& C, int B, size_t idx) {
     if (C.src == 1) return C.D64[B][idx];
     const float4 v = C.D32[B][idx];
-    if (C.src == 2 && v.z < 0.f) return C.D64[B][idx];
+    if (C.src == 2 && v.z < 0.f) {
+        const float4 f = reinterpret_cast<const float4*>(C.D64[B])[idx];
+        return make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+    }
     return make_double2((double)v.x, (double)v.y);
 }
 // |det|^2 er2 + zabs2 of an FP32 determinant (0 for one redone in FP64); an
@@ -924,6 +958,7 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
     }
     const bool want_err = C.err_coef > 0.0;
     const bool emit = want_err && !list && C.mlist[0] != nullptr;
+    const float floor_f = (float)C.p_floor, tol_f = (float)C.tol, ec_f = (float)C.err_coef;
     // per buffer: G_0 (n0), G_1 (n1) float4; A_0, A_1 (nsh each) float2; V (n0 + n1) float
     const size_t buf_words = (size_t)4 * (n0 + n1) + (size_t)4 * nsh + (emit ? (size_t)(n0 + n1) : 0);
     int it = 0;
@@ -964,11 +999,8 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
                 const float4 d = C.D32[B][idx];
                 errt[B][i] = want_err ? err_term_v(d) : 0.f;
                 float4 v = make_float4(d.x, 0.f, d.y, 0.f);
-                if (C.src == 2 && d.z < 0.f) {  // redone in FP64: as a float pair
-                    const double2 w = C.D64[B][idx];
-                    const float xh = (float)w.x, yh = (float)w.y;
-                    v = make_float4(xh, (float)(w.x - (double)xh), yh, (float)(w.y - (double)yh));
-                }
+                if (C.src == 2 && d.z < 0.f)  // redone in FP64, stored as a float pair
+                    v = reinterpret_cast<const float4*>(C.D64[B])[idx];
                 for (int pass = 0; pass < 2; ++pass)
                     for (int j = 0; j < rl; ++j) {
                         v = lane_butterfly(v, j, (e >> j) & 1);
@@ -1043,19 +1075,20 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
         }
         float budget = -1.f;
         if (lane == 0) {
-            const double ar = (double)a.x + (double)a.y, ai = (double)a.z + (double)a.w;
-            const double p = ar * ar + ai * ai;
-            out[b] = p;
+            // p = |amp|^2 in float pairs; one FP64 addition forms the output
+            const float2 pff = ff_add(ff_mul(make_float2(a.x, a.y), make_float2(a.x, a.y)),
+                                      ff_mul(make_float2(a.z, a.w), make_float2(a.z, a.w)));
+            out[b] = f2d_int(pff.x) + f2d_int(pff.y);
             // error estimate in FP32: |p~ - p| <= 2 |amp| s + s^2 for an amplitude error s
-            const float pf = (float)p, floor = (float)C.p_floor, tol = (float)C.tol, ec = (float)C.err_coef;
-            const float pm = fmaxf(pf, floor);
+            const float pf = pff.x, tol = tol_f, ec = ec_f;
+            const float pm = fmaxf(pf, floor_f);
             const float sp = sqrtf(pf);
             const float sig = ec * sqrtf(vv);
             const float e = want_err ? fmaf(2.f * sp, sig, sig * sig) / pm : 0.f;
             if (list) {
-                if (err) err[b] = -fabs(err[b]);
+                if (err) err[b] = neg_abs_int(err[b]);
             } else if (err) {
-                err[b] = (double)e;
+                err[b] = f2d_int(e);
             }
             if (append_list && !(e <= tol)) {
                 append_list[atomicAdd(append_count, 1)] = (int)b;
@@ -1118,7 +1151,7 @@ __device__ __forceinline__ void row_wht(T (&v)[1 << RL], Add add, Sub sub) {
 // shared memory holds F_B (float pairs), then A_B (FP32) and the variance
 // terms for the determinant list.
 template <int RL, int RPL>
-__global__ void __launch_bounds__(128) k_exact_combine_wp(ExactCombineDev C, const uint64_t* __restrict__ bits,
+__global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(ExactCombineDev C, const uint64_t* __restrict__ bits,
                                                           int64_t nb, int64_t stride, const int* __restrict__ list,
                                                           const int* __restrict__ list_count,
                                                           double* __restrict__ out, double* __restrict__ err,
@@ -1138,6 +1171,7 @@ __global__ void __launch_bounds__(128) k_exact_combine_wp(ExactCombineDev C, con
     }
     const bool want_err = C.err_coef > 0.0;
     const bool emit = want_err && !list && C.mlist[0] != nullptr;
+    const float floor_f = (float)C.p_floor, tol_f = (float)C.tol, ec_f = (float)C.err_coef;
     // per warp: G_0, G_1 (n0 + n1 float4; after step 2 reused for V, n0 + n1
     // float) | A_0, A_1 (2 nsh float2) or, when every s_B is one-to-one (C.inj),
     // Q_0, Q_1 (n0 + n1 float2) scattered in step 2
@@ -1176,11 +1210,8 @@ __global__ void __launch_bounds__(128) k_exact_combine_wp(ExactCombineDev C, con
                 const float4 d = C.D32[B][idx];
                 errt[rr][l] = want_err ? err_term_v(d) : 0.f;
                 v[l] = make_float4(d.x, 0.f, d.y, 0.f);
-                if (C.src == 2 && d.z < 0.f) {  // redone in FP64: as a float pair
-                    const double2 w = C.D64[B][idx];
-                    const float xh = (float)w.x, yh = (float)w.y;
-                    v[l] = make_float4(xh, (float)(w.x - (double)xh), yh, (float)(w.y - (double)yh));
-                }
+                if (C.src == 2 && d.z < 0.f)  // redone in FP64, stored as a float pair
+                    v[l] = reinterpret_cast<const float4*>(C.D64[B])[idx];
             }
             row_wht<RL>(v, cf_add, cf_sub);
             const float4* Wh = C.OmegaHatDF[B];
@@ -1261,19 +1292,20 @@ __global__ void __launch_bounds__(128) k_exact_combine_wp(ExactCombineDev C, con
         var = warp_sum_f(var);
         float budget = -1.f;
         if (lane == 0) {
-            const double ar = (double)acc.x + (double)acc.y, ai = (double)acc.z + (double)acc.w;
-            const double p = ar * ar + ai * ai;
-            out[b] = p;
+            // p = |amp|^2 in float pairs; one FP64 addition forms the output
+            const float2 pff = ff_add(ff_mul(make_float2(acc.x, acc.y), make_float2(acc.x, acc.y)),
+                                      ff_mul(make_float2(acc.z, acc.w), make_float2(acc.z, acc.w)));
+            out[b] = f2d_int(pff.x) + f2d_int(pff.y);
             // |p~ - p| <= 2 |amp| s + s^2 for an amplitude error s (in FP32)
-            const float pf = (float)p, tol = (float)C.tol, ec = (float)C.err_coef;
-            const float pm = fmaxf(pf, (float)C.p_floor);
+            const float pf = pff.x, tol = tol_f, ec = ec_f;
+            const float pm = fmaxf(pf, floor_f);
             const float sp = sqrtf(pf);
             const float sig = ec * sqrtf(var);
             const float e = want_err ? fmaf(2.f * sp, sig, sig * sig) / pm : 0.f;
             if (list) {
-                if (err) err[b] = -fabs(err[b]);
+                if (err) err[b] = neg_abs_int(err[b]);
             } else if (err) {
-                err[b] = (double)e;
+                err[b] = f2d_int(e);
             }
             if (append_list && !(e <= tol)) {
                 append_list[atomicAdd(append_count, 1)] = (int)b;
