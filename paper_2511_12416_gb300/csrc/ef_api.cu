@@ -912,8 +912,14 @@ int exact_enqueue_combine(ef_circuit* c, const ExactBuffers& eb, ef::ExactCombin
     for (int b = 0; b < c->nblocks; ++b) cm.mlist[b] = nullptr;
     cm.recomp = eb.recomp;
     if (per_minor) {
-        for (int b = 0; b < c->nblocks; ++b)
-            EF_CK(ef::launch_exact_lu_f64_minors(eb.blk[b], bits, eb.mlist[b], eb.count + 2 + b, nbb, s, st));
+        if (c->nblocks == 2 && eb.blk[0].eta == eb.blk[1].eta) {
+            EF_CK(ef::launch_exact_lu_f64_minors(eb.blk[0], eb.blk[1], 2, bits, eb.mlist[0], eb.mlist[1], eb.count + 2,
+                                                 nbb, s, st));
+        } else {
+            for (int b = 0; b < c->nblocks; ++b)
+                EF_CK(ef::launch_exact_lu_f64_minors(eb.blk[b], eb.blk[b], 1, bits, eb.mlist[b], nullptr,
+                                                     eb.count + 2 + b, nbb, s, st));
+        }
         ef::ExactCombineDev chk = cm;
         chk.src = 2;
         chk.col_by_index = 1;

@@ -312,22 +312,29 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const ui
 
 // Thread <-> one listed determinant (bitstring column, pattern z): redone in
 // FP64, stored in its D64 slot as a float pair (re hi, re lo, im hi, im lo),
-// and marked in D32 (er2 = -1).
+// and marked in D32 (er2 = -1). One launch covers the lists of nblk blocks of
+// the same particle count (items of block 1 follow those of block 0): the
+// run time is set by one warp's serial FP64 instruction stream, so a second
+// launch would double it.
 template <int ETA>
-__global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B, const uint64_t* __restrict__ bits,
-                                                       const int2* __restrict__ mlist,
+__global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B0, ExactBlockDev B1, int nblk,
+                                                       const uint64_t* __restrict__ bits,
+                                                       const int2* __restrict__ mlist0,
+                                                       const int2* __restrict__ mlist1,
                                                        const int* __restrict__ mcount, int64_t stride) {
-    const int64_t count = *mcount;
-    const int n = B.n;
+    const int64_t c0 = mcount[0];
+    const int64_t count = c0 + (nblk > 1 ? (int64_t)mcount[1] : 0);
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < count;
          item += (int64_t)gridDim.x * blockDim.x) {
-        const int2 e = mlist[item];
+        const bool second = item >= c0;
+        const ExactBlockDev& B = second ? B1 : B0;
+        const int2 e = second ? mlist1[item - c0] : mlist0[item];
         const int64_t pos = e.x;
         const int z = e.y;
         int rows[ETA];
         double2 res = make_double2(0.0, 0.0);
         if (decode_rows<ETA>(bits[2 * pos], bits[2 * pos + 1], B.mask0, B.mask1, rows)) {
-            const double2* Mz = B.M64 + (size_t)z * n * ETA;
+            const double2* Mz = B.M64 + (size_t)z * B.n * ETA;
             double2 A[ETA][ETA];
 #pragma unroll
             for (int i = 0; i < ETA; ++i)
@@ -343,24 +350,27 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B, const ui
 }
 
 template <int ETA>
-static cudaError_t launch_f64m_eta(const ExactBlockDev& b, const uint64_t* bits, const int2* mlist,
-                                   const int* mcount, int64_t stride, cudaStream_t s) {
-    k_exact_lu_f64m<ETA><<<152 * 8, 128, 0, s>>>(b, bits, mlist, mcount, stride);
+static cudaError_t launch_f64m_eta(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, const uint64_t* bits,
+                                   const int2* mlist0, const int2* mlist1, const int* mcount, int64_t stride,
+                                   cudaStream_t s) {
+    k_exact_lu_f64m<ETA><<<152 * 8, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_exact_lu_f64_minors(const ExactBlockDev& b, const uint64_t* bits, const int2* mlist,
+cudaError_t launch_exact_lu_f64_minors(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk,
+                                       const uint64_t* bits, const int2* mlist0, const int2* mlist1,
                                        const int* mcount, int64_t stride, cudaStream_t s, LaunchStats& st) {
+    if (nblk > 1 && b1.eta != b0.eta) return cudaErrorInvalidValue;
     cudaError_t e;
-    switch (b.eta) {
-        case 1: e = launch_f64m_eta<1>(b, bits, mlist, mcount, stride, s); break;
-        case 2: e = launch_f64m_eta<2>(b, bits, mlist, mcount, stride, s); break;
-        case 3: e = launch_f64m_eta<3>(b, bits, mlist, mcount, stride, s); break;
-        case 4: e = launch_f64m_eta<4>(b, bits, mlist, mcount, stride, s); break;
-        case 5: e = launch_f64m_eta<5>(b, bits, mlist, mcount, stride, s); break;
-        case 6: e = launch_f64m_eta<6>(b, bits, mlist, mcount, stride, s); break;
-        case 7: e = launch_f64m_eta<7>(b, bits, mlist, mcount, stride, s); break;
-        case 8: e = launch_f64m_eta<8>(b, bits, mlist, mcount, stride, s); break;
+    switch (b0.eta) {
+        case 1: e = launch_f64m_eta<1>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
+        case 2: e = launch_f64m_eta<2>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
+        case 3: e = launch_f64m_eta<3>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
+        case 4: e = launch_f64m_eta<4>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
+        case 5: e = launch_f64m_eta<5>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
+        case 6: e = launch_f64m_eta<6>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
+        case 7: e = launch_f64m_eta<7>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
+        case 8: e = launch_f64m_eta<8>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
         default: return cudaErrorInvalidValue;
     }
     st.launches += 1;
@@ -370,8 +380,9 @@ cudaError_t launch_exact_lu_f64_minors(const ExactBlockDev& b, const uint64_t* b
 template <int ETA>
 static cudaError_t launch_f64t_eta(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, const int* list,
                                    const int* list_count, int64_t stride, cudaStream_t s) {
+    // list mode: the list is usually short or empty, so a small grid strides over it
     const int64_t items = (list ? stride : nb) << b.r;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, 152 * 32));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, list ? 152 * 4 : 152 * 32));
     k_exact_lu_f64t<ETA><<<(unsigned)blocks, 128, 0, s>>>(b, bits, nb, list, list_count, stride);
     return cudaGetLastError();
 }
