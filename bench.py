@@ -38,6 +38,11 @@ import workloads as W  # noqa: E402
 METRIC = "Born-rule probabilities/s and branch-dets/s at rel err ≤1e-5 vs FP64 oracle"
 UNIT = "probabilities/s"
 NB = 10_000
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_exact_lu_f32<8> launch on this workload
+# (ncu, GB300, launches 7-12 of `bench.py --steps 3 --warmup 3 --no-cpu-baseline`): the pattern
+# matrices are read from L2 and the 41 MB of FP32 determinants stay in L2 until the combine.
+# To be re-measured whenever that kernel changes.
+LU_DRAM_BYTES_PER_LAUNCH = 468_224
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 L2_BYTES = 129 * 2 ** 20
 WORKLOAD = ("LUCJ exact: 2x16 modes (32 qubits), 8a+8b, k=16 controlled-phase gates "
@@ -308,14 +313,15 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "bitstrings_per_gpu": NB, "precision": args.precision,
-                   "arithmetic": "FP32 minors and LU, FP64 branch sums, FP64 recompute of flagged results",
+                   "arithmetic": "FP32 minors and LU, float-pair (~48-bit) branch sums, FP64 redo of the "
+                                 "determinants that carry a flagged result's estimated error",
                    "l2": "flushed between timed steps (2x L2 buffer written outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "branch_dets_per_s": branch_dets,
         "executed_lus_per_step": last["executed_minor_lus"],
         "fp64_recomputed_per_step": recomputed / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": LU_DRAM_BYTES_PER_LAUNCH,
                      "kernel": "k_exact_lu_f32 (FP32 LU of the per-block minors)",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
         "dominant_kernel_ms_per_step": kern_ms / args.steps,
