@@ -45,6 +45,7 @@ NB = 10_000
 LU_DRAM_BYTES_PER_LAUNCH = 468_224
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 L2_BYTES = 129 * 2 ** 20
+BATCH_TRAJ = 1000  # trajectories per Raw Estimate circuit of the batch workload
 WORKLOAD = ("LUCJ exact: 2x16 modes (32 qubits), 8a+8b, k=16 controlled-phase gates "
             "(4 aa + 4 bb neighbour, 8 ab on-site, N(0,0.1)), 2^16 branches, 10^4 sector bitstrings")
 
@@ -306,6 +307,27 @@ def run_ours(args):
                "sample": f"{len(idx)} of the 10^4 bitstrings ({per_core} per core), FP64 numpy oracle, "
                          f"one process per core; max rel err of the GPU results on them {max_rel:.2e}"}
 
+    # the plain FP64 single-circuit form on the same bitstrings (minors, LU and sums in FP64)
+    h64 = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
+    d_out64 = torch.empty(NB, dtype=torch.float64, device=dev)
+    steps64 = min(args.steps, 5)
+    ms64 = []
+    for i in range(1 + steps64):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ef.ef_prob_exact_dev(h64, d_bits.data_ptr(), NB, d_out64.data_ptr(), 0, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if i >= 1:
+            ms64.append(e0.elapsed_time(e1))
+    ef.ef_circuit_destroy(h64)
+    p64 = d_out64.cpu().numpy()
+    floor64 = 1e-6 / math.comb(16, 8) ** 2
+    fp64_form = {"value": NB / (statistics.mean(ms64) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(ms64),
+                 "steps": steps64, "form": "EF_PREC_FP64 single circuit, same bitstrings, L2 flushed",
+                 "max_rel_diff_of_value_results": float(np.max(np.abs(p_gpu - p64) / np.maximum(p64, floor64)))}
+
     kern_s = kern_ms / 1e3
     achieved = kern_flops / kern_s / 1e12 if kern_s > 0 else 0.0
     line = {
@@ -325,6 +347,7 @@ def run_ours(args):
                      "kernel": "k_exact_lu_f32 (FP32 LU of the per-block minors)",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
         "dominant_kernel_ms_per_step": kern_ms / args.steps,
+        "fp64_single_circuit": fp64_form,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": NB * 16, "d2h_bytes_per_step": NB * 8},
         "cpu_baseline": cpu,
@@ -338,6 +361,123 @@ def run_ours(args):
     return 0
 
 
+
+# ----------------------------------------------------------------------------- secondary workloads
+# (`--workload approx|grad|batch`): one JSON line each, device time with CUDA events, L2 flushed
+# between steps; the default run measures the Exact workload above.
+
+
+def _timed_steps(torch, dev, stream, flush, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def run_secondary(args):
+    import torch
+    import paper_2511_12416_gb300 as ef
+
+    ef.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic", "workload_kind": args.workload}
+    launches = 0
+    if args.workload == "approx":
+        c, bits = W.config3(args.nb)
+        h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP32_MINOR)
+        t = W.config3_trajectories(ef.ef_circuit_extent(h))
+        d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
+        d_out = torch.empty(len(bits), dtype=torch.float64, device=dev)
+        d_se = torch.empty(len(bits), dtype=torch.float64, device=dev)
+        seed = [0]
+
+        def fn():
+            seed[0] += 1
+            ef.ef_prob_approx_dev(h, d_bits.data_ptr(), len(bits), t, seed[0], 0, d_out.data_ptr(),
+                                  d_se.data_ptr(), stream.cuda_stream)
+        ms = _timed_steps(torch, dev, stream, flush, fn, args.steps, args.warmup)
+        launches = ef.ef_circuit_get_stats(h)["kernel_launches"]
+        ef.ef_circuit_destroy(h)
+        per = statistics.mean(ms)
+        line.update({"metric": "Raw Estimate probabilities/s (FP32 minors, FP64 trajectory sums)",
+                     "value": len(bits) / (per / 1e3), "unit": "probabilities/s", "ms_per_step": per,
+                     "dtype": "f32",
+                     "trajectories_per_s": len(bits) * t / (per / 1e3),
+                     "config": {"workload": f"LUCJ 52-qubit approximate: 2x26 modes, 5a+5b, 2 layers, k=152, "
+                                            f"t = ceil(extent/1e-4) = {t} trajectories per bitstring, "
+                                            f"{len(bits)} of the 10^5 sector bitstrings per step",
+                                "l2": "flushed between timed steps"}})
+    elif args.workload == "grad":
+        c, bits, w = W.config5()
+        h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
+        d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
+        d_gp = torch.empty(len(bits), dtype=torch.float64, device=dev)
+        d_p = torch.empty(len(bits), dtype=torch.float64, device=dev)
+        d_g = torch.empty(ef.ef_circuit_num_angles(h), dtype=torch.float64, device=dev)
+        ef.ef_prob_exact_dev(h, d_bits.data_ptr(), len(bits), d_p.data_ptr(), 0, stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        # d/dp of sum_b w_b log p_b
+        d_gp.copy_(torch.from_numpy(w).to(dev) / d_p.clamp_min(1e-300))
+
+        def fn():
+            ef.ef_prob_grad_dev(h, d_bits.data_ptr(), len(bits), d_gp.data_ptr(), d_p.data_ptr(), d_g.data_ptr(),
+                                stream.cuda_stream)
+        ms = _timed_steps(torch, dev, stream, flush, fn, args.steps, args.warmup)
+        launches = ef.ef_circuit_get_stats(h)["kernel_launches"]
+        n_ang = ef.ef_circuit_num_angles(h)
+        ef.ef_circuit_destroy(h)
+        per = statistics.mean(ms)
+        line.update({"metric": "bitstring gradients/s (d p_b / d every angle, FP64 adjoint)",
+                     "value": len(bits) / (per / 1e3), "unit": "bitstrings/s", "ms_per_step": per, "dtype": "f64",
+                     "config": {"workload": f"LUCJ 40-qubit: 2x20 modes, 6a+6b, 2 layers, k=12, {len(bits)} "
+                                            f"bitstrings, gradient of sum w_b log p_b w.r.t. {n_ang} angles",
+                                "l2": "flushed between timed steps"}})
+    else:  # batch
+        batch = W.config4()
+        hs, dbits, outs, nb, traj = [], [], [], [], []
+        for cc, bits, mode in batch:
+            hs.append(ef.ef_circuit_create(cc.n_modes, cc.occupation, cc.gates, precision=ef.EF_PREC_AUTO))
+            dbits.append(torch.from_numpy(bits.view(np.int64)).to(dev))
+            outs.append(torch.empty(len(bits), dtype=torch.float64, device=dev))
+            nb.append(len(bits))
+            traj.append(0 if mode == "exact" else BATCH_TRAJ)
+        b = ef.ef_batch_create(hs)
+        ptr_b, ptr_o = [d.data_ptr() for d in dbits], [o.data_ptr() for o in outs]
+
+        def fn():
+            ef.ef_batch_prob_dev(b, ptr_b, nb, ptr_o, traj, 7, stream.cuda_stream)
+        ms = _timed_steps(torch, dev, stream, flush, fn, args.steps, args.warmup)
+        launches = ef.ef_batch_get_stats(b)["kernel_launches"]
+        ef.ef_batch_destroy(b)
+        for h in hs:
+            ef.ef_circuit_destroy(h)
+        per = statistics.mean(ms)
+        n_exact = sum(1 for t in traj if t == 0)
+        line.update({"metric": "probabilities/s over an uneven 64-circuit batch (one captured graph)",
+                     "value": sum(nb) / (per / 1e3), "unit": "probabilities/s", "ms_per_step": per, "dtype": "f32",
+                     "circuits_per_s": len(hs) / (per / 1e3),
+                     "config": {"workload": f"64 circuits, n in 12..40, {sum(nb)} bitstrings, {n_exact} Exact "
+                                            f"(EF_PREC_AUTO), {len(hs) - n_exact} Raw Estimate with {BATCH_TRAJ} "
+                                            f"trajectories each; graph replay per step",
+                                "l2": "flushed between timed steps"}})
+    line["gpu_launches"] = launches
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global NB
     ap = argparse.ArgumentParser()
@@ -348,12 +488,16 @@ def main():
     ap.add_argument("--precision", choices=["auto", "fp64", "fp32"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nb", type=int, default=10_000, help="bitstrings per GPU (profiling runs use fewer)")
+    ap.add_argument("--workload", choices=["exact", "approx", "grad", "batch"], default="exact",
+                    help="exact: the headline line; the others measure the remaining paths, one line each")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     NB = args.nb
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "exact":
+        return run_secondary(args)
     return run_ours(args)
 
 
