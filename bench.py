@@ -42,7 +42,7 @@ NB = 10_000
 # (ncu, GB300, launches 7-12 of `bench.py --steps 3 --warmup 3 --no-cpu-baseline`): the pattern
 # matrices are read from L2 and the 41 MB of FP32 determinants stay in L2 until the combine.
 # To be re-measured whenever that kernel changes.
-LU_DRAM_BYTES_PER_LAUNCH = 468_224
+LU_DRAM_BYTES_PER_LAUNCH = None  # not yet re-measured for the bitstring-major layout
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 L2_BYTES = 129 * 2 ** 20
 BATCH_TRAJ = 1000  # trajectories per Raw Estimate circuit of the batch workload
@@ -210,6 +210,30 @@ def run_reference(args):
     return 0
 
 
+def time_fp64_form(ef, torch, c, d_bits, p_gpu, flush, stream, dev, steps):
+    """Device time of the EF_PREC_FP64 single-circuit form on the same bitstrings
+    and the largest relative difference of the headline results from it."""
+    h64 = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
+    d_out64 = torch.empty(NB, dtype=torch.float64, device=dev)
+    steps64 = min(steps, 5)
+    ms64 = []
+    for i in range(1 + steps64):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ef.ef_prob_exact_dev(h64, d_bits.data_ptr(), NB, d_out64.data_ptr(), 0, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if i >= 1:
+            ms64.append(e0.elapsed_time(e1))
+    ef.ef_circuit_destroy(h64)
+    p64 = d_out64.cpu().numpy()
+    floor64 = 1e-6 / math.comb(16, 8) ** 2
+    return {"value": NB / (statistics.mean(ms64) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(ms64),
+            "steps": steps64, "form": "EF_PREC_FP64 single circuit, same bitstrings, L2 flushed",
+            "max_rel_diff_of_value_results": float(np.max(np.abs(p_gpu - p64) / np.maximum(p64, floor64)))}
+
+
 def run_ours(args):
     import torch
 
@@ -308,25 +332,9 @@ def run_ours(args):
                          f"one process per core; max rel err of the GPU results on them {max_rel:.2e}"}
 
     # the plain FP64 single-circuit form on the same bitstrings (minors, LU and sums in FP64)
-    h64 = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
-    d_out64 = torch.empty(NB, dtype=torch.float64, device=dev)
-    steps64 = min(args.steps, 5)
-    ms64 = []
-    for i in range(1 + steps64):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ef.ef_prob_exact_dev(h64, d_bits.data_ptr(), NB, d_out64.data_ptr(), 0, stream.cuda_stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if i >= 1:
-            ms64.append(e0.elapsed_time(e1))
-    ef.ef_circuit_destroy(h64)
-    p64 = d_out64.cpu().numpy()
-    floor64 = 1e-6 / math.comb(16, 8) ** 2
-    fp64_form = {"value": NB / (statistics.mean(ms64) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(ms64),
-                 "steps": steps64, "form": "EF_PREC_FP64 single circuit, same bitstrings, L2 flushed",
-                 "max_rel_diff_of_value_results": float(np.max(np.abs(p_gpu - p64) / np.maximum(p64, floor64)))}
+    fp64_form = None
+    if not args.no_fp64_form:
+        fp64_form = time_fp64_form(ef, torch, c, d_bits, p_gpu, flush, stream, dev, args.steps)
 
     kern_s = kern_ms / 1e3
     achieved = kern_flops / kern_s / 1e12 if kern_s > 0 else 0.0
@@ -487,6 +495,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "fp64", "fp32"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the FP64 single-circuit form")
     ap.add_argument("--nb", type=int, default=10_000, help="bitstrings per GPU (profiling runs use fewer)")
     ap.add_argument("--workload", choices=["exact", "approx", "grad", "batch"], default="exact",
                     help="exact: the headline line; the others measure the remaining paths, one line each")

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
                 const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
                 res = make_float4(det.x, det.y, er2, zabs2);
             }
-            B.D32[z * nb + b] = res;
+            B.D32[dix(b, (uint32_t)z, B.r)] = res;
         }
     }
 }
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restri
                     const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
                     res = make_float4(det.x, det.y, er2, zabs2);
                 }
-                B.D32[z * E.nb + b] = res;
+                B.D32[dix(b, (uint32_t)z, B.r)] = res;
             }
         }
         __syncthreads();
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const ui
                 for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
             res = lu_det_plain<double, ETA>(A);
         }
-        B.D64[(size_t)z * stride + pos] = res;
+        B.D64[dix(pos, (uint32_t)z, B.r)] = res;
     }
 }
 
@@ -343,9 +343,9 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B0, ExactBl
             res = lu_det_plain<double, ETA>(A);
         }
         const float xh = (float)res.x, yh = (float)res.y;
-        reinterpret_cast<float4*>(B.D64)[(size_t)z * stride + pos] =
+        reinterpret_cast<float4*>(B.D64)[dix(pos, (uint32_t)z, B.r)] =
             make_float4(xh, (float)(res.x - (double)xh), yh, (float)(res.y - (double)yh));
-        B.D32[(size_t)z * stride + pos] = make_float4(0.f, 0.f, -1.f, 0.f);
+        B.D32[dix(pos, (uint32_t)z, B.r)] = make_float4(0.f, 0.f, -1.f, 0.f);
     }
 }
 
@@ -431,9 +431,9 @@ __global__ void __launch_bounds__(256) k_exact_lu_rows(ExactBlockDev B, const ui
             const T det = lu_det_rows<R, G>(rowv, r, eta, er2, zabs2);
             if (valid && r == 0) {
                 if constexpr (std::is_same<R, double>::value)
-                    B.D64[z * stride + pos] = ok ? det : make_double2(0.0, 0.0);
+                    B.D64[dix(pos, (uint32_t)z, B.r)] = ok ? det : make_double2(0.0, 0.0);
                 else
-                    B.D32[z * stride + pos] = ok ? make_float4(det.x, det.y, er2, zabs2)
+                    B.D32[dix(pos, (uint32_t)z, B.r)] = ok ? make_float4(det.x, det.y, er2, zabs2)
                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
@@ -743,7 +743,7 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
             // amp = sum_z Omega(z) det(z); C(z) = Omega(z)
             const int nz = 1 << C.r[0];
             for (int z = tid; z < nz; z += NT) {
-                const size_t idx = (size_t)z * stride + col;
+                const size_t idx = dix(col, (uint32_t)z, C.r[0]);
                 const double2 v = det_at(C, 0, idx);
                 const double2 w = C.Omega[0][z];
                 ar = fma(w.x, v.x, fma(-w.y, v.y, ar));
@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
                 float4* GB = B ? G1 : G0;
                 const int nz = 1 << C.r[B];
                 for (int z = tid; z < nz; z += NT) {
-                    const float4 v = C.D32[B][(size_t)z * stride + col];
+                    const float4 v = C.D32[B][dix(col, (uint32_t)z, C.r[B])];
                     GB[z] = make_float4(v.x, 0.f, v.y, 0.f);
                 }
             }
@@ -789,7 +789,7 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
             for (int B = 0; B < 2; ++B) {
                 double2* FB = B ? F1 : F0;
                 const int nz = 1 << C.r[B];
-                for (int z = tid; z < nz; z += NT) FB[z] = det_at(C, B, (size_t)z * stride + col);
+                for (int z = tid; z < nz; z += NT) FB[z] = det_at(C, B, dix(col, (uint32_t)z, C.r[B]));
             }
             __syncthreads();
             // forward transform (the last stage also multiplies by the transformed
@@ -824,7 +824,7 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
                     const int nl = B == 0 ? nl0 : nl1;
                     double sx = 0.0, sy = 0.0;
                     for (int zl = 0; zl < nl; ++zl) {
-                        const double2 v = det_at(C, B, (size_t)(zl ^ sB) * stride + col);
+                        const double2 v = det_at(C, B, dix(col, (uint32_t)zl ^ sB, C.r[B]));
                         const double2 w = C.Omega[B][zl];
                         sx = fma(w.x, v.x, fma(-w.y, v.y, sx));
                         sy = fma(w.x, v.y, fma(w.y, v.x, sy));
@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
                         cx += t.x;
                         cy += t.y;
                     }
-                    const float vt = fmaf(cx, cx, cy * cy) * err_term(C, B, (size_t)z * stride + col);
+                    const float vt = fmaf(cx, cx, cy * cy) * err_term(C, B, dix(col, (uint32_t)z, C.r[B]));
                     var += vt;
                     if (emit) smV[B * voff1 + z] = vt;
                 }
@@ -1006,7 +1006,7 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
             for (int i = 0; i < kWregMax; ++i) {
                 const int e = tid + NT * i;
                 if (e >= nz) break;
-                const size_t idx = (size_t)e * stride + col;
+                const size_t idx = dix(col, (uint32_t)e, C.r[B]);
                 const float4 d = C.D32[B][idx];
                 errt[B][i] = want_err ? err_term_v(d) : 0.f;
                 float4 v = make_float4(d.x, 0.f, d.y, 0.f);
@@ -1217,7 +1217,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
             float4 v[NL];
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
-                const size_t idx = (size_t)(z0 | l) * stride + col;
+                const size_t idx = dix(col, (uint32_t)(z0 | l), C.r[B]);
                 const float4 d = C.D32[B][idx];
                 errt[rr][l] = want_err ? err_term_v(d) : 0.f;
                 v[l] = make_float4(d.x, 0.f, d.y, 0.f);

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_grad_combine(GradDev G, const uint64_t*
                 ar = tid == 0 ? 1.0 : 0.0;
             } else if (C.nblocks == 1) {
                 for (int z = tid; z < (1 << C.r[0]); z += NT) {
-                    const double2 v = C.D64[0][(size_t)z * nb + b];
+                    const double2 v = C.D64[0][dix(b, (uint32_t)z, C.r[0])];
                     const double2 w = C.Omega[0][z];
                     ar = fma(w.x, v.x, fma(-w.y, v.y, ar));
                     ai = fma(w.x, v.y, fma(w.y, v.x, ai));
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_grad_combine(GradDev G, const uint64_t*
                         const uint32_t sB = C.s[B][xs];
                         double sx = 0.0, sy = 0.0;
                         for (int zl = 0; zl < (1 << C.r_loc[B]); ++zl) {
-                            const double2 v = C.D64[B][(size_t)(zl ^ sB) * nb + b];
+                            const double2 v = C.D64[B][dix(b, (uint32_t)zl ^ sB, C.r[B])];
                             const double2 w = C.Omega[B][zl];
                             sx = fma(w.x, v.x, fma(-w.y, v.y, sx));
                             sy = fma(w.x, v.y, fma(w.y, v.x, sy));
@@ -130,11 +130,11 @@ __global__ void __launch_bounds__(256) k_grad_combine(GradDev G, const uint64_t*
                 double2 e = make_double2(0.0, 0.0);
                 if (ok) {
                     if (C.nblocks == 1) {
-                        const double2 v = C.D64[0][(size_t)zl * nb + b];
+                        const double2 v = C.D64[0][dix(b, (uint32_t)zl, C.r[0])];
                         e = make_double2(v.x, v.y);
                     } else {
                         for (int xs = 0; xs < nsh; ++xs) {
-                            const double2 v = C.D64[B][(size_t)((uint32_t)zl ^ C.s[B][xs]) * nb + b];
+                            const double2 v = C.D64[B][dix(b, (uint32_t)zl ^ C.s[B][xs], C.r[B])];
                             const double2 t = cm2(C.WS[xs], cm2(Aoth[xs], make_double2(v.x, v.y)));
                             e.x += t.x;
                             e.y += t.y;

@@ -40,10 +40,16 @@ struct ExactBlockDev {
     const uint32_t* F;      // L x n: flip masks over pattern bits
     double2* M64;           // 2^r x n x eta branch matrices (FP64)
     float2* M32;            // same, FP32 (may be null)
-    // determinants per (pattern, bitstring column), [2^r][stride] each:
+    // determinants per (bitstring column, pattern), [stride][2^r] each (dix):
     float4* D32;            // FP32 LU: (det re, det im, er2, zabs2); er2 < 0 marks one redone in D64
     double2* D64;           // FP64 LU: det
 };
+
+// Index of the determinant of pattern z (of 2^r) for bitstring column col in
+// D32 / D64: bitstring-major, so one bitstring's 2^r determinants are
+// contiguous (coalesced reads by the combine; the LU's threads each write a
+// run of consecutive patterns).
+__host__ __device__ inline size_t dix(int64_t col, uint32_t z, int r) { return ((size_t)col << r) + z; }
 
 // amp(b) = sum_{x_sh} WS[x_sh] prod_B A_B(x_sh),
 // A_B(x_sh) = sum_{z < 2^r_loc} Omega_B[z] det_B(z ^ s_B[x_sh]).
