@@ -779,7 +779,16 @@ void exact_block_geometry(const ef_circuit* c, int b, int64_t cap, ef::ExactBloc
     d.L = B.L;
     d.r = B.r;
     d.r_loc = B.r_loc;
-    d.c_log2 = ef::exact_f32_chunk_log2(B.n, B.eta, B.r, cap);
+    // ef_options.tile_override[0] > 0 fixes the patterns per chunk (log2), within the
+    // pattern count and 96 KiB of staged matrices
+    int cl = c->opt.tile_override[0];
+    if (cl > 0) {
+        cl = std::min(cl, B.r);
+        while (cl > 0 && ((size_t)1 << cl) * B.n * (size_t)(B.eta | 1) * sizeof(float2) > 96 * 1024) --cl;
+    } else {
+        cl = ef::exact_f32_chunk_log2(B.n, B.eta, B.r, cap);
+    }
+    d.c_log2 = cl;
     d.n_chunks = 1 << (B.r - d.c_log2);
     d.mask0 = B.mask[0];
     d.mask1 = B.mask[1];
