@@ -153,17 +153,20 @@ __global__ void __launch_bounds__(256) k_grad_combine(GradDev G, const uint64_t*
 
 // ---------------------------------------------------------------- minor adjoints per pattern
 
-// Inverse and determinant by Gauss-Jordan elimination with partial pivoting
-// (FP64, thread per matrix; the rows are exchanged through local memory).
+// In-place Gauss-Jordan inversion with partial (row) pivoting: A becomes
+// A^{-1}, the return value is det(A) (0 for an exactly singular pivot column,
+// A then undefined). Each step scales the pivot row and clears column k in all
+// other rows, N^3 complex multiply-adds in all (half of the work of reducing
+// [A | I]); the row interchanges are undone on the inverse's columns in
+// reverse order.
 template <int N>
-__device__ __forceinline__ double2 inv_det(double2 (&A)[N][N], double2 (&Inv)[N][N]) {
-    for (int i = 0; i < N; ++i)
-        for (int j = 0; j < N; ++j) Inv[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+__device__ __forceinline__ double2 inv_det_inplace(double2 (&A)[N][N]) {
     double2 det = make_double2(1.0, 0.0);
     bool odd = false;
+    int perm[N];
     for (int k = 0; k < N; ++k) {
-        int p = k;
         double best = abs2(A[k][k]);
+        int p = k;
         for (int i = k + 1; i < N; ++i) {
             const double m = abs2(A[i][k]);
             if (m > best) {
@@ -172,41 +175,40 @@ __device__ __forceinline__ double2 inv_det(double2 (&A)[N][N], double2 (&Inv)[N]
             }
         }
         if (best == 0.0) return make_double2(0.0, 0.0);
+        perm[k] = p;
         if (p != k) {
             odd = !odd;
             for (int j = 0; j < N; ++j) {
                 const double2 t = A[k][j];
                 A[k][j] = A[p][j];
                 A[p][j] = t;
-                const double2 u = Inv[k][j];
-                Inv[k][j] = Inv[p][j];
-                Inv[p][j] = u;
             }
         }
         const double2 piv = A[k][k];
         det = cm2(det, piv);
         const double ib = 1.0 / best;
         const double2 ip = make_double2(piv.x * ib, -piv.y * ib);
-        for (int j = 0; j < N; ++j) {
-            A[k][j] = cm2(A[k][j], ip);
-            Inv[k][j] = cm2(Inv[k][j], ip);
-        }
+        A[k][k] = make_double2(1.0, 0.0);
+        for (int j = 0; j < N; ++j) A[k][j] = cm2(A[k][j], ip);
         for (int i = 0; i < N; ++i) {
             if (i == k) continue;
             const double2 f = A[i][k];
-            for (int j = 0; j < N; ++j) {
-                A[i][j] = cfms(A[i][j], f, A[k][j]);
-                Inv[i][j] = cfms(Inv[i][j], f, Inv[k][j]);
-            }
+            A[i][k] = make_double2(0.0, 0.0);
+            for (int j = 0; j < N; ++j) A[i][j] = cfms(A[i][j], f, A[k][j]);
+        }
+    }
+    for (int k = N - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p == k) continue;
+        for (int i = 0; i < N; ++i) {
+            const double2 t = A[i][k];
+            A[i][k] = A[i][p];
+            A[i][p] = t;
         }
     }
     return odd ? make_double2(-det.x, -det.y) : det;
 }
 
-// Cofactor (i, j) of an N x N matrix given by its row pointers: (-1)^{i+j}
-// times the determinant of the matrix without row i and column j (LU with
-// partial pivoting on the (N-1) x (N-1) remainder). Used when the minor is
-// exactly singular, where the adjugate is still needed.
 template <int N>
 __device__ double2 cofactor(const double2* __restrict__ Mz, const int (&rows)[N], int i0, int j0) {
     constexpr int K = N - 1;
@@ -272,33 +274,33 @@ __global__ void __launch_bounds__(128) k_grad_minors(GradDev G, int blk, const u
         const int64_t b = t0 + tid;
         int rows[ETA];
         uint64_t lm = 0;
-        double2 Gm[ETA][ETA];
         bool ok = false;
+        double2* gt = gs + (size_t)tid * ETA * ETA;
         if (b < nb) {
             ok = decode_rows<ETA>(bits[2 * b], bits[2 * b + 1], B.mask0, B.mask1, rows);
             const double2 cb = cot[b];
             ok = ok && (cb.x != 0.0 || cb.y != 0.0);
             if (ok) {
-                double2 A[ETA][ETA], Inv[ETA][ETA];
+                double2 A[ETA][ETA];
                 for (int i = 0; i < ETA; ++i) {
                     lm |= 1ull << rows[i];
                     for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
                 }
-                const double2 det = inv_det<ETA>(A, Inv);
+                const double2 det = inv_det_inplace<ETA>(A);
                 if (det.x != 0.0 || det.y != 0.0) {
-                    // Gm[i][j] = cot det Inv[j][i] = cot adj(A)_{ji} = cot d det / dA_ij
+                    // G[i][j] = cot det (A^{-1})[j][i] = cot adj(A)_{ji} = cot d det / dA_ij
                     const double2 f = cm2(cb, det);
                     for (int i = 0; i < ETA; ++i)
-                        for (int j = 0; j < ETA; ++j) Gm[i][j] = cm2(f, Inv[j][i]);
+                        for (int j = 0; j < ETA; ++j) gt[i * ETA + j] = cm2(f, A[j][i]);
                 } else {
                     for (int i = 0; i < ETA; ++i)
-                        for (int j = 0; j < ETA; ++j) Gm[i][j] = cm2(cb, cofactor<ETA>(Mz, rows, i, j));
+                        for (int j = 0; j < ETA; ++j) gt[i * ETA + j] = cm2(cb, cofactor<ETA>(Mz, rows, i, j));
                 }
             }
         }
         rmask[tid] = ok ? lm : 0ull;
-        for (int i = 0; i < ETA; ++i)
-            for (int j = 0; j < ETA; ++j) gs[((size_t)tid * ETA + i) * ETA + j] = ok ? Gm[i][j] : make_double2(0.0, 0.0);
+        if (!ok)
+            for (int e = 0; e < ETA * ETA; ++e) gt[e] = make_double2(0.0, 0.0);
         __syncthreads();
         // fixed-order accumulation: element (m, j) sums the tile's threads in order
         for (int e = tid; e < ne; e += NT) {
