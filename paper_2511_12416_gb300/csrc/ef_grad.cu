@@ -432,24 +432,40 @@ cudaError_t launch_grad(const GradDev& g, const uint64_t* bits, int64_t nb, cons
 
 // ---------------------------------------------------------------- fixed-order sums
 // out[e] = sum_{k < count} in[k * stride + e] for e < width (complex), k ascending.
-__global__ void k_sum_rows(const double2* __restrict__ in, int64_t count, int64_t stride, int64_t width,
-                           double2* __restrict__ out) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < width; e += (int64_t)gridDim.x * blockDim.x) {
-        double ax = 0.0, ay = 0.0;
-        for (int64_t k = 0; k < count; ++k) {
+// out[e] = sum_k in[k * stride + e] for e < width, in a fixed order: a CTA
+// covers 32 consecutive e (one per lane); warp w adds rows w, w + 32, w + 64,
+// ... and warp 0 then adds the 32 warps' partial sums in order. Splitting the
+// count over 32 warps keeps the chains of dependent FP64 additions short.
+__global__ void __launch_bounds__(1024) k_sum_rows(const double2* __restrict__ in, int64_t count, int64_t stride,
+                                                   int64_t width, double2* __restrict__ out) {
+    __shared__ double2 part[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    double ax = 0.0, ay = 0.0;
+    if (e < width)
+        for (int64_t k = w; k < count; k += 32) {
             const double2 v = in[k * stride + e];
             ax += v.x;
             ay += v.y;
         }
-        out[e] = make_double2(ax, ay);
+    part[w][lane] = make_double2(ax, ay);
+    __syncthreads();
+    if (w == 0 && e < width) {
+        double sx = 0.0, sy = 0.0;
+        for (int q = 0; q < 32; ++q) {
+            sx += part[q][lane].x;
+            sy += part[q][lane].y;
+        }
+        out[e] = make_double2(sx, sy);
     }
 }
 
 cudaError_t launch_sum_rows(const double2* in, int64_t count, int64_t stride, int64_t width, double2* out,
                             cudaStream_t s, LaunchStats& st) {
     if (width <= 0) return cudaSuccess;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((width + 255) / 256, 152 * 16));
-    k_sum_rows<<<(unsigned)blocks, 256, 0, s>>>(in, count, stride, width, out);
+    const int64_t blocks = (width + 31) / 32;
+    if (blocks > 2147483647ll) return cudaErrorInvalidValue;
+    k_sum_rows<<<(unsigned)blocks, 1024, 0, s>>>(in, count, stride, width, out);
     st.launches += 1;
     return cudaGetLastError();
 }
