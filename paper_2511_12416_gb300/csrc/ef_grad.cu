@@ -125,23 +125,38 @@ __global__ void __launch_bounds__(256) k_grad_combine(GradDev G, const uint64_t*
                 }
                 G.cot[B][(size_t)z * nb + b] = cm2(gam, cz);
             }
-            const int nzl = 1 << C.r_loc[B];
-            for (int zl = tid; zl < nzl; zl += NT) {
-                double2 e = make_double2(0.0, 0.0);
-                if (ok) {
-                    if (C.nblocks == 1) {
-                        const double2 v = C.D64[0][dix(b, (uint32_t)zl, C.r[0])];
-                        e = make_double2(v.x, v.y);
-                    } else {
-                        for (int xs = 0; xs < nsh; ++xs) {
-                            const double2 v = C.D64[B][dix(b, (uint32_t)zl ^ C.s[B][xs], C.r[B])];
-                            const double2 t = cm2(C.WS[xs], cm2(Aoth[xs], make_double2(v.x, v.y)));
-                            e.x += t.x;
-                            e.y += t.y;
-                        }
-                    }
+            if (C.nblocks == 1) {
+                const int nzl = 1 << C.r_loc[0];
+                for (int zl = tid; zl < nzl; zl += NT) {
+                    const double2 v = ok ? C.D64[0][dix(b, (uint32_t)zl, C.r[0])] : make_double2(0.0, 0.0);
+                    G.ebar[0][(size_t)b * nzl + zl] = cm2(gam, v);
                 }
-                G.ebar[B][(size_t)b * nzl + zl] = cm2(gam, e);
+            }
+        }
+        if (C.nblocks == 2) {
+            // E_B(zl) = sum_xs w_sh(xs) A_other(xs) det_B(zl ^ s_B(xs)): one warp per
+            // (block, zl), lanes over xs, then a butterfly (full warps: on this GPU an
+            // FP64 instruction costs the same with one active lane as with 32)
+            const int lane = tid & 31, warp = tid >> 5;
+            const int nz0 = 1 << C.r_loc[0], nz1 = 1 << C.r_loc[1];
+            for (int pr = warp; pr < nz0 + nz1; pr += NT / 32) {
+                const int B = pr < nz0 ? 0 : 1;
+                const int zl = B ? pr - nz0 : pr;
+                const double2* Aoth = smA + (1 - B) * nsh;
+                double ex = 0.0, ey = 0.0;
+                if (ok)
+                    for (int xs = lane; xs < nsh; xs += 32) {
+                        const double2 v = C.D64[B][dix(b, (uint32_t)zl ^ C.s[B][xs], C.r[B])];
+                        const double2 t = cm2(C.WS[xs], cm2(Aoth[xs], v));
+                        ex += t.x;
+                        ey += t.y;
+                    }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    ex += __shfl_xor_sync(0xffffffffu, ex, off);
+                    ey += __shfl_xor_sync(0xffffffffu, ey, off);
+                }
+                if (lane == 0) G.ebar[B][(size_t)b * (B ? nz1 : nz0) + zl] = cm2(gam, make_double2(ex, ey));
             }
         }
         if (C.nblocks == 2)
