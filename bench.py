@@ -72,7 +72,7 @@ def _oracle_worker(task):
 
 
 def make_workload(rank: int = 0):
-    c, _ = W.config2(0)
+    c, _ = W.lucj32_exact(0)
     rng = np.random.default_rng(replica_plan(rank, 1, NB)[0])
     bits = W.spin_sector_bitstrings(16, 8, 8, NB, rng)
     return c, bits
@@ -405,9 +405,9 @@ def run_secondary(args):
             "vs_baseline": None, "data": "synthetic", "workload_kind": args.workload}
     launches = 0
     if args.workload == "approx":
-        c, bits = W.config3(args.nb)
+        c, bits = W.lucj52_approx(args.nb)
         h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP32_MINOR)
-        t = W.config3_trajectories(ef.ef_circuit_extent(h))
+        t = W.lucj52_trajectories(ef.ef_circuit_extent(h))
         d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
         d_out = torch.empty(len(bits), dtype=torch.float64, device=dev)
         d_se = torch.empty(len(bits), dtype=torch.float64, device=dev)
@@ -430,7 +430,7 @@ def run_secondary(args):
                                             f"{len(bits)} of the 10^5 sector bitstrings per step",
                                 "l2": "flushed between timed steps"}})
     elif args.workload == "grad":
-        c, bits, w = W.config5()
+        c, bits, w = W.lucj40_grad()
         h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
         d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
         d_gp = torch.empty(len(bits), dtype=torch.float64, device=dev)
@@ -455,7 +455,7 @@ def run_secondary(args):
                                             f"bitstrings, gradient of sum w_b log p_b w.r.t. {n_ang} angles",
                                 "l2": "flushed between timed steps"}})
     else:  # batch
-        batch = W.config4()
+        batch = W.uneven_batch64()
         hs, dbits, outs, nb, traj = [], [], [], [], []
         for cc, bits, mode in batch:
             hs.append(ef.ef_circuit_create(cc.n_modes, cc.occupation, cc.gates, precision=ef.EF_PREC_AUTO))

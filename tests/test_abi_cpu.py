@@ -70,7 +70,7 @@ def test_invalid_circuits_are_rejected(ef, recs, occ, msg):
 
 
 def test_angle_layout_and_extent_match_oracle(ef):
-    for c in (W.config1()[0], W.config2(16)[0], W.config3(4)[0], W.config5(8)[0]):
+    for c in (W.brick8_exact()[0], W.lucj32_exact(16)[0], W.lucj52_approx(4)[0], W.lucj40_grad(8)[0]):
         h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates)
         try:
             assert np.array_equal(ef.ef_circuit_get_angles(h), O.get_angles(c.gates))

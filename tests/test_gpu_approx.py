@@ -31,7 +31,7 @@ def run_approx(lib, c, bits, t, seed, precision, index_base=0):
 
 
 CASES = [
-    ("config1", lambda: W.config1(), 3000),
+    ("brick8_exact", lambda: W.brick8_exact(), 3000),
     ("random-n10-eta4-k7", lambda: (W.random_fig4_circuit(10, 4, 7, 3, seed=31, angle_std=1.2),
                                     W.sector_bitstrings_all(10, 4)[:60]), 1000),
     ("lucj-12q", lambda: (W.lucj_circuit(6, 3, 3, 1, n_onsite=6, n_same=3, angle_sampler=W.normal_var(0.1),
@@ -63,14 +63,14 @@ def test_approx_matches_oracle_same_trajectories(lib, name, maker, t, prec):
 
 
 def test_approx_global_index_and_subsets(lib):
-    c, bits = W.config1()
+    c, bits = W.brick8_exact()
     p_all, se_all, _ = run_approx(lib, c, bits, 500, 7, lib.EF_PREC_FP64)
     p_sub, se_sub, _ = run_approx(lib, c, bits[30:45], 500, 7, lib.EF_PREC_FP64, index_base=30)
     assert np.array_equal(p_sub, p_all[30:45]) and np.array_equal(se_sub, se_all[30:45])
 
 
 def test_approx_zero_angles_is_exact(lib):
-    c, bits = W.config1()
+    c, bits = W.brick8_exact()
     recs = [(int(g["kind"]), int(g["p"]), int(g["q"]), 0.0 if int(g["kind"]) == W.CPHASE else float(g["theta"]),
              float(g["phi"])) for g in c.gates]
     c0 = W.Circuit(8, c.occupation, W.make_gates(recs))
@@ -80,7 +80,7 @@ def test_approx_zero_angles_is_exact(lib):
 
 
 def test_approx_edge_cases(lib):
-    c, bits = W.config1()
+    c, bits = W.brick8_exact()
     bad = np.array([W.modes_to_bits([0, 1]), W.modes_to_bits([0, 1, 2, 3, 4])], dtype=np.uint64)
     p, se, _ = run_approx(lib, c, bad, 100, 0, lib.EF_PREC_FP32_MINOR)
     assert np.all(p == 0) and np.all(se == 0)
@@ -108,11 +108,11 @@ def test_approx_unbiased_against_exact(lib):
     assert abs(z) < 4.0
 
 
-def test_approx_config3_full_trajectory_count_sampled(lib):
-    """Config 3 (52 modes, k=152, t = ceil(extent/eps^2)) at full t on 256
+def test_approx_lucj52_approx_full_trajectory_count_sampled(lib):
+    """The 52-qubit LUCJ workload (k=152, t = ceil(extent/eps^2)) at full t on 256
     bitstrings; the oracle checks two of them."""
-    c, bits = W.config3(256)
-    t = W.config3_trajectories(O.extent(c.gates))
+    c, bits = W.lucj52_approx(256)
+    t = W.lucj52_trajectories(O.extent(c.gates))
     p, se, st = run_approx(lib, c, bits, t, 0, lib.EF_PREC_FP32_MINOR)
     idx = [0, 201]
     p_ref, se_ref = O.raw_estimate(c, bits[idx], t=t, seed=0, b_indices=idx)

@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 def _small_batch():
     rng = np.random.default_rng(8)
     out = []
-    out.append((W.config1()[0], W.config1()[1], 0))
+    out.append((W.brick8_exact()[0], W.brick8_exact()[1], 0))
     out.append((W.lucj_circuit(6, 3, 3, 1, n_onsite=6, n_same=3, angle_sampler=W.normal_var(0.1), seed=7),
                 W.spin_sector_bitstrings_all(6, 3, 3), 0))
     out.append((W.lucj_circuit(5, 2, 2, 2, n_onsite=3, n_same=2, angle_sampler=W.normal_var(0.5), seed=8),
@@ -79,11 +79,11 @@ def test_batch_equals_individual_calls_and_replays(lib):
             lib.ef_circuit_destroy(h)
 
 
-def test_batch_config4_subset(lib):
+def test_batch_uneven64_subset(lib):
     """The 64 uneven circuits of the batch workload, 300 bitstrings each and
     200 trajectories for the approximate ones: the batch matches the
     individual calls, and the oracle on sampled exact results."""
-    batch = W.config4()
+    batch = W.uneven_batch64()
     hs, dbits, outs, nb, traj = [], [], [], [], []
     for c, bits, mode in batch:
         hs.append(lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_AUTO))

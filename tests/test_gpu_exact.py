@@ -40,7 +40,7 @@ def run_exact(lib, c, bits, precision, want_err=False, **kw):
 
 
 SMALL = [
-    ("config1", lambda: W.config1()),
+    ("brick8_exact", lambda: W.brick8_exact()),
     ("brick-after", lambda: (W.brick_circuit(8, 4, 3, seed=0, cphase_between=False), W.sector_bitstrings_all(8, 4))),
     ("random-n10-eta5-k6", lambda: (W.random_fig4_circuit(10, 5, 6, 3, seed=22), W.sector_bitstrings_all(10, 5))),
     ("random-n12-eta1-k4", lambda: (W.random_fig4_circuit(12, 1, 4, 2, seed=24), W.sector_bitstrings_all(12, 1))),
@@ -87,7 +87,7 @@ def test_exact_fp32_error_estimate_bounds_error(lib, name, maker):
 
 
 def test_exact_edge_cases(lib):
-    c, bits = W.config1()
+    c, bits = W.brick8_exact()
     # wrong Hamming weight -> exactly 0; empty call; ragged count
     bad = np.array([W.modes_to_bits([0, 1, 2]), W.modes_to_bits([0, 1, 2, 3, 4]), W.modes_to_bits([])],
                    dtype=np.uint64)
@@ -133,10 +133,10 @@ def test_exact_sector_sums_to_one_all_precisions(lib):
         assert abs(p.sum() - 1.0) < tol
 
 
-def test_exact_config2_full_size_sampled(lib):
+def test_exact_lucj32_exact_full_size_sampled(lib):
     """10^4 bitstrings in the bench's launch configuration; the oracle checks
     a sample (first, last and random positions) and the FP64 path checks all."""
-    c, bits = W.config2()
+    c, bits = W.lucj32_exact()
     floor = 1e-6 / sector_size(c)
     (p_auto, err), st = run_exact(lib, c, bits, lib.EF_PREC_AUTO, want_err=True)
     p64, _ = run_exact(lib, c, bits, lib.EF_PREC_FP64)
@@ -149,11 +149,11 @@ def test_exact_config2_full_size_sampled(lib):
     assert st["logical_branch_dets"] == len(bits) * 2 ** 16
 
 
-@pytest.mark.parametrize("which", ["config2", "config5"])
+@pytest.mark.parametrize("which", ["lucj32_exact", "lucj40_grad"])
 def test_exact_fp32_estimate_on_full_size_workloads(lib, which):
     """At full size the FP32 path's estimate bounds its error against the
     (oracle-checked) FP64 path, and EF_PREC_AUTO meets 1e-5 everywhere."""
-    c, bits = W.config2() if which == "config2" else W.config5()[:2]
+    c, bits = W.lucj32_exact() if which == "lucj32_exact" else W.lucj40_grad()[:2]
     floor = 1e-6 / sector_size(c)
     p64, _ = run_exact(lib, c, bits, lib.EF_PREC_FP64)
     (p32, err), _ = run_exact(lib, c, bits, lib.EF_PREC_FP32_MINOR, want_err=True)
@@ -166,7 +166,7 @@ def test_exact_fp32_estimate_on_full_size_workloads(lib, which):
 
 def test_exact_repeatable_and_device_api(lib):
     torch = pytest.importorskip("torch")
-    c, bits = W.config2(1000)
+    c, bits = W.lucj32_exact(1000)
     h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_AUTO)
     try:
         p_host = lib.ef_prob_exact(h, bits)

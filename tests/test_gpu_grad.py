@@ -25,7 +25,7 @@ def gpu_grad(lib, c, bits, g):
 
 
 SMALL = [
-    ("config1", lambda: W.config1()),
+    ("brick8_exact", lambda: W.brick8_exact()),
     ("random-n8-eta3-k5", lambda: (W.random_fig4_circuit(8, 3, 5, 2, seed=21), W.sector_bitstrings_all(8, 3))),
     ("random-n10-eta4-k6-sparse", lambda: (W.random_fig4_circuit(10, 4, 6, 1, seed=23, angle_std=2.0),
                                            W.sector_bitstrings_all(10, 4)[:80])),
@@ -48,7 +48,7 @@ def test_grad_matches_oracle_all_angles(lib, name, maker):
 
 
 def test_grad_edge_cases(lib):
-    c, bits = W.config1()
+    c, bits = W.brick8_exact()
     na = len(O.get_angles(c.gates))
     p, grad = gpu_grad(lib, c, np.zeros((0, 2), dtype=np.uint64), np.zeros(0))
     assert len(p) == 0 and np.all(grad == 0) and len(grad) == na
@@ -62,10 +62,10 @@ def _log_weights(p, w):
     return w / p
 
 
-def test_grad_config5_subset_against_oracle(lib):
-    """Config 5's circuit (2x20 modes, 6a+6b, 2 layers, k=12) on 12 bitstrings:
+def test_grad_lucj40_grad_subset_against_oracle(lib):
+    """The 40-qubit LUCJ gradient circuit (2x20 modes, 6a+6b, 2 layers, k=12) on 12 bitstrings:
     random directions and sampled components against the oracle."""
-    c, bits, w = W.config5()
+    c, bits, w = W.lucj40_grad()
     sub = bits[:12]
     p_ref = O.exact_probabilities(c, sub)
     g = w[:12] / p_ref
@@ -83,10 +83,10 @@ def test_grad_config5_subset_against_oracle(lib):
     assert np.max(np.abs(grad[idx] - ref)) <= 1e-9 * scale
 
 
-def test_grad_config5_full_against_finite_differences(lib):
+def test_grad_lucj40_grad_full_against_finite_differences(lib):
     """All 4096 bitstrings, L = sum_b w_b log p_b, adjoint against central
     differences (h = 1e-6) of the GPU FP64 forward pass."""
-    c, bits, w = W.config5()
+    c, bits, w = W.lucj40_grad()
     h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_FP64)
     try:
         p = lib.ef_prob_exact(h, bits)

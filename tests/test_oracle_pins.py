@@ -88,7 +88,7 @@ def test_cphase_decomposition_identity():
 
 
 @pytest.mark.parametrize("maker", [
-    lambda: W.config1(),
+    lambda: W.brick8_exact(),
     lambda: (W.brick_circuit(8, 4, 3, seed=0, cphase_between=False), W.sector_bitstrings_all(8, 4)),
     lambda: (W.random_fig4_circuit(8, 3, 5, 2, seed=21), W.sector_bitstrings_all(8, 3)),
     lambda: (W.random_fig4_circuit(10, 5, 6, 3, seed=22), W.sector_bitstrings_all(10, 5)),
@@ -127,7 +127,7 @@ def test_two_layer_lucj_matches_statevector():
 
 
 def test_wrong_weight_bitstring_has_zero_probability():
-    c, _ = W.config1()
+    c, _ = W.brick8_exact()
     bits = np.array([W.modes_to_bits([0, 1, 2]), W.modes_to_bits([0, 1, 2, 3, 4])], dtype=np.uint64)
     assert np.all(O.exact_probabilities(c, bits) == 0.0)
 
@@ -167,7 +167,7 @@ def test_givens_network_reproduces_the_unitary():
 
 
 def test_zero_angle_cphase_is_identity_and_angles_wrap():
-    base, bits = W.config1()
+    base, bits = W.brick8_exact()
     recs = [(int(g["kind"]), int(g["p"]), int(g["q"]), float(g["theta"]), float(g["phi"])) for g in base.gates]
     p0 = O.exact_probabilities(base, bits)
     with_zero = W.Circuit(8, base.occupation, W.make_gates(recs[:5] + [(W.CPHASE, 1, 6, 0.0, 0.0)] + recs[5:]))
@@ -178,7 +178,7 @@ def test_zero_angle_cphase_is_identity_and_angles_wrap():
 
 
 def test_cphase_next_to_basis_states_does_not_change_probabilities():
-    base, bits = W.config1()
+    base, bits = W.brick8_exact()
     recs = [(int(g["kind"]), int(g["p"]), int(g["q"]), float(g["theta"]), float(g["phi"])) for g in base.gates]
     nocp = [r for r in recs if r[0] != W.CPHASE]
     p_ref = O.exact_probabilities(W.Circuit(8, base.occupation, W.make_gates(nocp)), bits)
@@ -250,7 +250,7 @@ def test_trajectory_bound_eq6_limits():
 
 
 def test_raw_estimate_zero_angles_is_exact():
-    c, bits = W.config1()
+    c, bits = W.brick8_exact()
     recs = [(int(g["kind"]), int(g["p"]), int(g["q"]), 0.0 if int(g["kind"]) == W.CPHASE else float(g["theta"]),
              float(g["phi"])) for g in c.gates]
     c0 = W.Circuit(8, c.occupation, W.make_gates(recs))
@@ -289,7 +289,7 @@ def test_raw_estimate_converges_and_stderr_is_calibrated():
 
 
 def test_trajectories_depend_only_on_global_index():
-    c, bits = W.config1()
+    c, bits = W.brick8_exact()
     X1 = O.sample_trajectories(c, b_index=12345678901, t=64, seed=9)
     X2 = O.sample_trajectories(c, b_index=12345678901, t=64, seed=9)
     X3 = O.sample_trajectories(c, b_index=12345678902, t=64, seed=9)

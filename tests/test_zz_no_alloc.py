@@ -27,11 +27,11 @@ def _floor(c):
 
 
 CASES = [
-    ("config1", lambda: W.config1()),
+    ("brick8_exact", lambda: W.brick8_exact()),
     ("lucj-12q", lambda: (W.lucj_circuit(6, 3, 3, 1, n_onsite=6, n_same=3,
                                          angle_sampler=W.normal_var(0.1, math.pi), seed=7),
                           W.spin_sector_bitstrings_all(6, 3, 3))),
-    ("lucj-32q-1500", lambda: W.config2(1500)),
+    ("lucj-32q-1500", lambda: W.lucj32_exact(1500)),
 ]
 
 
@@ -61,7 +61,7 @@ def test_noalloc_matches_allocating_entry_point_twice(lib, name, maker, prec, to
 
 
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch(lib):
-    c, _ = W.config2(0)
+    c, _ = W.lucj32_exact(0)
     nb = 200_000
     # real buffers of the full size, so that the call would be valid if it ran
     bits = W.spin_sector_bitstrings(16, 8, 8, 64, np.random.default_rng(0))

@@ -281,14 +281,14 @@ def sector_bitstrings(n_modes: int, eta: int, count: int, rng: np.random.Generat
 # The five workload configurations
 # ---------------------------------------------------------------------------
 
-def config1() -> tuple[Circuit, np.ndarray]:
+def brick8_exact() -> tuple[Circuit, np.ndarray]:
     """Exact mode, FP64: 8 modes, eta=4 in modes 0-3, one brick layer (seed 0),
     k=3 controlled-phase gates with angles in [0, pi/4]; all 70 bitstrings."""
     c = brick_circuit(8, 4, 3, seed=0)
     return c, sector_bitstrings_all(8, 4)
 
 
-def config2(n_bitstrings: int = 10_000) -> tuple[Circuit, np.ndarray]:
+def lucj32_exact(n_bitstrings: int = 10_000) -> tuple[Circuit, np.ndarray]:
     """LUCJ-shaped exact mode: 2x16 modes, 8a+8b, one Jastrow layer of k=16
     (4 aa + 4 bb nearest-neighbour, 8 ab on-site) with angles N(0, 0.1)
     between a Haar rotation and its inverse; bitstrings uniform in (8,8)."""
@@ -298,7 +298,7 @@ def config2(n_bitstrings: int = 10_000) -> tuple[Circuit, np.ndarray]:
     return c, bits
 
 
-def config3(n_bitstrings: int = 100_000) -> tuple[Circuit, np.ndarray]:
+def lucj52_approx(n_bitstrings: int = 100_000) -> tuple[Circuit, np.ndarray]:
     """Approximate mode: 2x26 modes, 5a+5b, 2-layer LUCJ with 26 on-site +
     25 aa + 25 bb controlled-phase gates per layer (k=152), angles uniform in
     [-0.05, 0.05]; bitstrings uniform in (5,5)."""
@@ -308,12 +308,12 @@ def config3(n_bitstrings: int = 100_000) -> tuple[Circuit, np.ndarray]:
     return c, bits
 
 
-def config3_trajectories(extent: float, eps: float = 1e-2, cap: int = 1_000_000) -> int:
+def lucj52_trajectories(extent: float, eps: float = 1e-2, cap: int = 1_000_000) -> int:
     """t = ceil(extent * eps^-2), capped."""
     return int(min(math.ceil(extent / (eps * eps)), cap))
 
 
-def config5(n_bitstrings: int = 4096) -> tuple[Circuit, np.ndarray, np.ndarray]:
+def lucj40_grad(n_bitstrings: int = 4096) -> tuple[Circuit, np.ndarray, np.ndarray]:
     """Differentiation: 2x20 modes, 6a+6b, 2-layer LUCJ with k=12 (per layer
     4 on-site + 1 aa + 1 bb), angles N(0, 0.1); 4096 sector bitstrings and
     weights uniform in [0, 1]."""
@@ -325,7 +325,7 @@ def config5(n_bitstrings: int = 4096) -> tuple[Circuit, np.ndarray, np.ndarray]:
     return c, bits, w
 
 
-def config4(n_circuits: int = 64, seed: int = 4) -> list[tuple[Circuit, np.ndarray, str]]:
+def uneven_batch64(n_circuits: int = 64, seed: int = 4) -> list[tuple[Circuit, np.ndarray, str]]:
     """Uneven batch: n uniform in even {12..40} (n/2 orbitals per spin), eta per
     spin uniform in [2, n/3], k uniform in [4, 24] with angles N(0, 0.1),
     1-3 Givens brick layers per spin, bitstrings per circuit log-uniform in
