@@ -113,6 +113,7 @@ struct HostBlock {
     int k_loc = 0;
     std::vector<int> local_gates;  // cphase indices local to the block
     int r = 0, r_loc = 0;          // rank of the flip patterns / of the local gates' patterns
+    int r_sign = 0;                // rank of the patterns of gates that only change minors' signs
     std::vector<uint32_t> F;       // L x n: flip masks over pattern bits
     std::vector<cd> Omega;         // 2^r_loc: weights of the local gates folded onto patterns
     std::vector<float2> Omega32;   // FP32 copy (error estimate)
@@ -459,6 +460,60 @@ int prepare(ef_circuit* c) {
         B.r = (int)basis.size();
         B.coord = coord;
         B.local_of = local_of;
+        // Gates whose flips only change signs of this block's minors: at the
+        // first layer, flips of rows of S_0[:, C] that leave the support of every
+        // column wholly flipped or wholly not (one sign per column); at the last
+        // layer, flips of columns of S_L that do the same for every row (one sign
+        // per row of the minor). Minors of patterns that differ by such gates
+        // are one FP32 computation up to sign, so their rounding errors add
+        // coherently: over the 2^r_sign patterns these gates span (r_sign the
+        // rank of their patterns) by at most 2^(r_sign / 2) times the estimate's
+        // independent sum (Cauchy-Schwarz), which fp32_err_coef applies.
+        {
+            const cd* S0 = &B.S[0];
+            const cd* SL = &B.S[(size_t)L * nn];
+            std::vector<char> fl((size_t)nb_);
+            auto sign_only = [&](int jj) {
+                const CP& cp = c->cps[jj];
+                const int l = layer_of_cp[jj] - 1;
+                std::fill(fl.begin(), fl.end(), 0);
+                bool any = false;
+                if (cp.blk_p == b) fl[local_of[cp.p]] ^= 1, any = true;
+                if (cp.blk_q == b) fl[local_of[cp.q]] ^= 1, any = true;
+                if (l < 0 || !any) return false;
+                bool first_ok = l == 0, last_ok = l == L - 1;
+                for (int cc = 0; first_ok && cc < B.eta; ++cc) {
+                    bool f = false, u = false;
+                    for (int i = 0; i < nb_; ++i)
+                        if (S0[(size_t)i * nb_ + B.cols[cc]] != cd(0, 0)) (fl[i] ? f : u) = true;
+                    first_ok = !(f && u);
+                }
+                for (int i = 0; last_ok && i < nb_; ++i) {
+                    bool f = false, u = false;
+                    for (int m = 0; m < nb_; ++m)
+                        if (SL[(size_t)i * nb_ + m] != cd(0, 0)) (fl[m] ? f : u) = true;
+                    last_ok = !(f && u);
+                }
+                return first_ok || last_ok;
+            };
+            std::vector<std::vector<uint64_t>> sech;  // echelon of the sign-only patterns
+            std::vector<int> spiv;
+            for (int jj : gates_B) {
+                if (!sign_only(jj)) continue;
+                std::vector<uint64_t> v = pattern(jj);
+                for (size_t e = 0; e < sech.size(); ++e)
+                    if ((v[spiv[e] >> 6] >> (spiv[e] & 63)) & 1ull)
+                        for (int w = 0; w < PW; ++w) v[w] ^= sech[e][w];
+                int piv = -1;
+                for (int w = 0; w < PW && piv < 0; ++w)
+                    if (v[w]) piv = w * 64 + __builtin_ctzll(v[w]);
+                if (piv >= 0) {
+                    sech.push_back(v);
+                    spiv.push_back(piv);
+                }
+            }
+            B.r_sign = (int)sech.size();
+        }
         if (too_many || B.k_loc > ef::kMaxExactLocalBits || (c->nblocks == 2 && k_sh > ef::kMaxExactSharedBits)) {
             c->exact_ok = false;
             c->exact_why = "Exact mode: a mode block needs more than 2^" + std::to_string(ef::kMaxExactPatternBits) +
@@ -862,11 +917,16 @@ ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
 // whose standard deviation is about a third of the K = 1 estimate, so K = 4
 // bounds them at about 5 standard deviations (the largest ratio seen in
 // 16,000 significant results was 0.76 at K = 4); ef_options.tile_override[1]
-// > 0 sets K in tenths.
+// > 0 sets K in tenths. Minors that are one computation up to sign are not
+// independent: for a block with r_sign such pattern directions the coefficient
+// takes a factor 2^(r_sign / 2) (one for circuits whose controlled-phase gates
+// all sit between rotations).
 double fp32_err_coef(const ef_circuit* c) {
     if (c->opt.precision == EF_PREC_FP64) return 0.0;
     const double K = c->opt.tile_override[1] > 0 ? 0.1 * c->opt.tile_override[1] : 4.0;
-    return K * std::ldexp(1.0, -24);
+    int rs = 0;  // coherent rounding errors of minors equal up to sign (HostBlock::r_sign)
+    for (int b = 0; b < c->nblocks; ++b) rs = std::max(rs, c->blk[b].r_sign);
+    return K * std::ldexp(1.0, -24) * std::sqrt(std::ldexp(1.0, rs));
 }
 
 void exact_account(ef_circuit* c, int64_t nb) {

@@ -19,10 +19,13 @@ template <typename R> using cplx_t = typename V2<R>::T;
 __host__ __device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
 __host__ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
 
+// The fused form is written out so that every kernel that inlines this rounds
+// the same way (left to the compiler, which product is fused can depend on the
+// surrounding code).
 template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
     T r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
+    r.x = fma(a.x, b.x, -(a.y * b.y));
+    r.y = fma(a.x, b.y, a.y * b.x);
     return r;
 }
 // a - l * p
@@ -45,6 +48,22 @@ template <typename T> __device__ __forceinline__ auto abs2(T a) -> decltype(a.x)
 
 __device__ __forceinline__ float recip(float m) { return __frcp_rn(m); }
 __device__ __forceinline__ double recip(double m) { return 1.0 / m; }
+// Smallest |pivot|^2 the eliminations divide by (the smallest normal number):
+// below it 1/|p|^2 overflows and a zero component of the pivot turns the
+// multipliers into NaN (0 * inf). Such a pivot counts as zero; the error
+// proxy's zero-pivot term then covers the determinant, whose size is below
+// the rounding error of any entry of its column. Minors of the FP32 path meet
+// such pivots when rounding noise stands where an exact zero belongs.
+__device__ __forceinline__ float min_pivot2(float) { return 1.17549435e-38f; }
+__device__ __forceinline__ double min_pivot2(double) { return 2.2250738585072014e-308; }
+// 1/u^2 for the unit roundoff u of the type (2^-24, 2^-53)
+__device__ __forceinline__ float inv_u2(float) { return 281474976710656.0f; }
+__device__ __forceinline__ double inv_u2(double) { return 81129638414606681695789005144064.0; }
+// One pivot's term (k+1) c_k^2 / |u_kk|^2 of the error proxy er2 (units of
+// u^2), raised to 1/u^2 (relative error 1) once it exceeds 1/(16 u^2).
+template <typename R> __device__ __forceinline__ R pivot_err_term(R t) {
+    return t > R(0.0625) * inv_u2(R(0)) ? fmax(t, inv_u2(R(0))) : t;
+}
 
 // multiply by i^ph (ph in 0..3)
 __device__ __forceinline__ double2 times_i_pow(double2 a, int ph) {
@@ -148,11 +167,15 @@ __device__ __forceinline__ int nth_row(uint64_t w0, uint64_t w1, uint64_t m0, ui
 // path. Pivot u_kk is formed by k+1 rounded updates of entries no larger than
 // the original column's largest entry c_k, so its relative error is about
 // sqrt(k+1) u c_k / |u_kk|; the determinant's relative error squared is then
-// er2 = sum_k (k+1) c_k^2 / |u_kk|^2 (in units of u^2). A pivot that is
-// exactly zero leaves det = 0 with an absolute error of about
+// er2 = sum_k (k+1) c_k^2 / |u_kk|^2 (in units of u^2). A zero pivot (|u_kk|^2
+// below the smallest normal number) leaves det ~ 0 with an absolute error of about
 // sqrt(k+1) u c_k prod_{j != k} |u_jj|; zabs2 is the square of that (0 when no
-// pivot vanished). The elimination steps are a compile-time recursion so every
-// matrix index is a constant and the matrix stays in registers.
+// pivot vanished). A pivot whose own term puts its relative error above 1/4 is
+// rounding noise (the minor is singular up to rounding, and the accumulated
+// error of such a pivot was seen up to ~4x its term): its term becomes 1/u^2,
+// a relative error of 1 for the determinant. The elimination steps are a
+// compile-time recursion so every matrix index is a constant and the matrix
+// stays in registers.
 // Rows K+1.. minus l_i times the pivot row K, l_i = A[i][K] / pivot (ip = 1/pivot).
 // In FP32 on sm_100+ each complex update a - l p is two packed FP32x2 FMAs,
 // (a.x, a.y) + (-l.x, -l.x)(p.x, p.y) + (l.y, -l.y)(p.y, p.x).
@@ -171,14 +194,15 @@ __device__ __forceinline__ void eliminate(cplx_t<R> (&A)[N][N], cplx_t<R> ip) {
 #pragma unroll
             for (int j = K + 1; j < N; ++j) A[i][j] = __ffma2_rn(ly, psw[j], __ffma2_rn(nl, A[K][j], A[i][j]));
         }
-        return;
-    }
+    } else
 #endif
+    {
 #pragma unroll
-    for (int i = K + 1; i < N; ++i) {
-        const cplx_t<R> l = cmul(A[i][K], ip);
+        for (int i = K + 1; i < N; ++i) {
+            const cplx_t<R> l = cmul(A[i][K], ip);
 #pragma unroll
-        for (int j = K + 1; j < N; ++j) A[i][j] = cfms(A[i][j], l, A[K][j]);
+            for (int j = K + 1; j < N; ++j) A[i][j] = cfms(A[i][j], l, A[K][j]);
+        }
     }
 }
 
@@ -218,9 +242,9 @@ __device__ __forceinline__ void lu_step(cplx_t<R> (&A)[N][N], const R (&cm2)[N],
         for (int j = K; j < N; ++j) A[K][j] = prow[j];
         const T piv = A[K][K];
         d = cmul(d, piv);
-        const bool nz = best > R(0);
+        const bool nz = best >= min_pivot2(R(0));
         const R inv = nz ? recip(best) : R(0);
-        er2 = fma(R(K + 1) * cm2[K], inv, er2);
+        er2 += pivot_err_term(R(K + 1) * cm2[K] * inv);
         pz *= nz ? best : R(1);
         zc = nz ? zc : R(K + 1) * cm2[K];
         nzero += nz ? 0 : 1;
@@ -286,7 +310,7 @@ __device__ __forceinline__ void lu_step_plain(cplx_t<R> (&A)[N][N], cplx_t<R>& d
         for (int j = K; j < N; ++j) A[K][j] = prow[j];
         const T piv = A[K][K];
         d = cmul(d, piv);
-        const R inv = best > R(0) ? recip(best) : R(0);
+        const R inv = best >= min_pivot2(R(0)) ? recip(best) : R(0);
         const T ip = mk(piv.x * inv, -piv.y * inv);
         eliminate<R, N, K>(A, ip);
         lu_step_plain<R, N, K + 1>(A, d, odd);
@@ -354,9 +378,9 @@ __device__ __forceinline__ cplx_t<R> lu_det_rows(cplx_t<R> (&row)[G], int r, int
         piv.y = __shfl_sync(full, row[k].y, p, G);
         const R best = mag;
         d = cmul(d, piv);
-        const bool nz = best > R(0);
+        const bool nz = best >= min_pivot2(R(0));
         const R invm = nz ? recip(best) : R(0);
-        er2 = fma(R(k + 1) * cm, invm, er2);
+        er2 += pivot_err_term(R(k + 1) * cm * invm);
         pz *= nz ? best : R(1);
         zc = nz ? zc : R(k + 1) * cm;
         nzero += nz ? 0 : 1;

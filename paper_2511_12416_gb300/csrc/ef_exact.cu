@@ -14,7 +14,8 @@
 //
 //   1. k_build_branches : U_B(z)[:, C_B] for every pattern z (dense FP64 products);
 //   2. k_exact_lu_*     : det U_B(z)[R_B(b), C_B] (Eq. 3) for every (pattern, bitstring),
-//                         LU with partial pivoting, plus a rounding-error proxy;
+//                         LU with partial pivoting, plus a rounding-error proxy
+//                         (the FP32 kernels are in ef_lu32.cu);
 //   3. k_exact_combine  : amp(b) = sum_{x_sh} w_sh(x_sh) prod_B A_B(x_sh) with
 //                         A_B(x_sh) = sum_{z local} Omega_B(z) det_B(z ^ s_B(x_sh)),
 //                         p(b) = |amp|^2, and the FP32 path's error estimate.
@@ -85,197 +86,6 @@ cudaError_t launch_build_branches(const ExactBlockDev& b, bool want32, cudaStrea
     k_build_branches<<<grid, 128, smem, s>>>(b, want32 ? 1 : 0);
     st.launches += 1;
     return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- 2a. FP32, thread per minor
-// Thread <-> bitstring; the CTA stages one chunk of 2^c_log2 pattern matrices
-// (row stride ETA|1 float2 so that the rows of a matrix fall in distinct
-// banks) and every thread factors its own minor of each, in registers.
-
-int exact_f32_chunk_log2(int n, int eta, int r, int64_t nb) {
-    int cl = std::min(r, 5);
-    while (cl > 0 && ((size_t)1 << cl) * n * (size_t)(eta | 1) * sizeof(float2) > 48 * 1024) --cl;
-    // keep at least ~5 waves of 3 CTAs per SM (measured on the 32-qubit workload:
-    // 8 patterns per chunk beat 4 by 2 % and 16 lose 5 %)
-    const int64_t tiles = (nb + 127) / 128;
-    while (cl > 0 && tiles * ((int64_t)1 << (r - cl)) < 152 * 3 * 5) --cl;
-    return cl;
-}
-
-template <int ETA>
-__global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uint64_t* __restrict__ bits,
-                                                      int64_t nb) {
-    extern __shared__ float2 smM[];
-    constexpr int S = ETA | 1;
-    const int n = B.n;
-    const int Y = 1 << B.c_log2;
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int rows[ETA];
-    const bool ok = (b < nb) && decode_rows<ETA>(bits[2 * b], bits[2 * b + 1], B.mask0, B.mask1, rows);
-    for (int chunk = blockIdx.y; chunk < B.n_chunks; chunk += gridDim.y) {
-        const float2* src = B.M32 + (size_t)chunk * Y * n * ETA;
-        __syncthreads();
-        for (int e = threadIdx.x; e < Y * n * ETA; e += blockDim.x) {
-            const int row = e / ETA, j = e - row * ETA;
-            smM[row * S + j] = src[e];
-        }
-        __syncthreads();
-        if (b >= nb) continue;
-        for (int t = 0; t < Y; ++t) {
-            const size_t z = (size_t)chunk * Y + t;
-            float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (ok) {
-                const float2* Mt = smM + (size_t)t * n * S;
-                float2 A[ETA][ETA];
-#pragma unroll
-                for (int i = 0; i < ETA; ++i) {
-                    const float2* rp = Mt + rows[i] * S;
-#pragma unroll
-                    for (int j = 0; j < ETA; ++j) A[i][j] = rp[j];
-                }
-                float er2, zabs2;
-                const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
-                res = make_float4(det.x, det.y, er2, zabs2);
-            }
-            B.D32[dix(b, (uint32_t)z, B.r)] = res;
-        }
-    }
-}
-
-template <int ETA>
-static cudaError_t launch_f32_eta(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, cudaStream_t s) {
-    constexpr int S = ETA | 1;
-    const size_t smem = (size_t)(1 << b.c_log2) * b.n * S * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_exact_lu_f32<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((nb + 127) / 128), (unsigned)std::min(b.n_chunks, 65535));
-    k_exact_lu_f32<ETA><<<grid, 128, smem, s>>>(b, bits, nb);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_exact_lu_f32(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, cudaStream_t s,
-                                LaunchStats& st) {
-    if (nb <= 0) return cudaSuccess;
-    cudaError_t e;
-    switch (b.eta) {
-        case 1: e = launch_f32_eta<1>(b, bits, nb, s); break;
-        case 2: e = launch_f32_eta<2>(b, bits, nb, s); break;
-        case 3: e = launch_f32_eta<3>(b, bits, nb, s); break;
-        case 4: e = launch_f32_eta<4>(b, bits, nb, s); break;
-        case 5: e = launch_f32_eta<5>(b, bits, nb, s); break;
-        case 6: e = launch_f32_eta<6>(b, bits, nb, s); break;
-        case 7: e = launch_f32_eta<7>(b, bits, nb, s); break;
-        case 8: e = launch_f32_eta<8>(b, bits, nb, s); break;
-        case 9: e = launch_f32_eta<9>(b, bits, nb, s); break;
-        case 10: e = launch_f32_eta<10>(b, bits, nb, s); break;
-        default: return cudaErrorInvalidValue;
-    }
-    st.launches += 1;
-    st.executed_lus += nb * ((int64_t)1 << b.r);
-    return e;
-}
-
-// ---------------------------------------------------------------- 2a'. FP32 work queue over several circuits
-// Persistent kernel for a batch of circuits whose blocks share eta: every CTA
-// repeatedly takes the next (circuit block, bitstring tile, pattern chunk)
-// item from a device counter, stages that chunk's matrices and factors the
-// minors of its 128 bitstrings exactly as k_exact_lu_f32 does. CTAs leave
-// when the queue is empty (no CTA ever waits for another).
-
-template <int ETA>
-__global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restrict__ q, int nq, int64_t n_items,
-                                                      unsigned long long* __restrict__ head) {
-    extern __shared__ float2 smQ[];
-    __shared__ long long s_item;
-    constexpr int S = ETA | 1;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(head, 1ull);
-        __syncthreads();
-        const int64_t item = s_item;
-        __syncthreads();
-        if (item >= n_items) break;
-        int lo = 0, hi = nq - 1;  // last entry with item_begin <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (q[mid].item_begin <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        const QueueEntry& E = q[lo];
-        const ExactBlockDev& B = E.blk;
-        const int64_t local = item - E.item_begin;
-        const int chunk = (int)(local / E.tiles);
-        const int64_t tile = local - (int64_t)chunk * E.tiles;
-        const int n = B.n;
-        const int Y = 1 << B.c_log2;
-        const float2* src = B.M32 + (size_t)chunk * Y * n * ETA;
-        for (int e = threadIdx.x; e < Y * n * ETA; e += blockDim.x) {
-            const int row = e / ETA, j = e - row * ETA;
-            smQ[row * S + j] = src[e];
-        }
-        __syncthreads();
-        const int64_t b = tile * 128 + threadIdx.x;
-        if (b < E.nb) {
-            int rows[ETA];
-            const bool ok = decode_rows<ETA>(E.bits[2 * b], E.bits[2 * b + 1], B.mask0, B.mask1, rows);
-            for (int t = 0; t < Y; ++t) {
-                const size_t z = (size_t)chunk * Y + t;
-                float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ok) {
-                    const float2* Mt = smQ + (size_t)t * n * S;
-                    float2 A[ETA][ETA];
-#pragma unroll
-                    for (int i = 0; i < ETA; ++i) {
-                        const float2* rp = Mt + rows[i] * S;
-#pragma unroll
-                        for (int j = 0; j < ETA; ++j) A[i][j] = rp[j];
-                    }
-                    float er2, zabs2;
-                    const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
-                    res = make_float4(det.x, det.y, er2, zabs2);
-                }
-                B.D32[dix(b, (uint32_t)z, B.r)] = res;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-template <int ETA>
-static cudaError_t launch_queue_eta(const QueueEntry* q, int nq, int64_t n_items, unsigned long long* head,
-                                    size_t smem, int grid, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_queue_lu_f32<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (grid <= 0) {  // one wave of resident CTAs
-        int dev = 0, sms = 0, occ = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_queue_lu_f32<ETA>, 128, smem)) != cudaSuccess)
-            return e;
-        grid = sms * std::max(1, occ);
-    }
-    k_queue_lu_f32<ETA><<<grid, 128, smem, s>>>(q, nq, n_items, head);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_queue_lu_f32(int eta, const QueueEntry* q, int nq, int64_t n_items, unsigned long long* head,
-                                size_t smem, int grid, cudaStream_t s, LaunchStats& st) {
-    if (n_items <= 0 || nq <= 0) return cudaSuccess;
-    cudaError_t e;
-    switch (eta) {
-        case 1: e = launch_queue_eta<1>(q, nq, n_items, head, smem, grid, s); break;
-        case 2: e = launch_queue_eta<2>(q, nq, n_items, head, smem, grid, s); break;
-        case 3: e = launch_queue_eta<3>(q, nq, n_items, head, smem, grid, s); break;
-        case 4: e = launch_queue_eta<4>(q, nq, n_items, head, smem, grid, s); break;
-        case 5: e = launch_queue_eta<5>(q, nq, n_items, head, smem, grid, s); break;
-        case 6: e = launch_queue_eta<6>(q, nq, n_items, head, smem, grid, s); break;
-        case 7: e = launch_queue_eta<7>(q, nq, n_items, head, smem, grid, s); break;
-        case 8: e = launch_queue_eta<8>(q, nq, n_items, head, smem, grid, s); break;
-        case 9: e = launch_queue_eta<9>(q, nq, n_items, head, smem, grid, s); break;
-        case 10: e = launch_queue_eta<10>(q, nq, n_items, head, smem, grid, s); break;
-        default: return cudaErrorInvalidValue;
-    }
-    st.launches += 1;
-    return e;
 }
 
 // ---------------------------------------------------------------- 2b. FP64, thread per minor

@@ -227,43 +227,46 @@ __device__ __forceinline__ double2 inv_det_inplace(double2 (&A)[N][N]) {
 template <int N>
 __device__ double2 cofactor(const double2* __restrict__ Mz, const int (&rows)[N], int i0, int j0) {
     constexpr int K = N - 1;
-    if (K == 0) return make_double2(1.0, 0.0);
-    double2 S[K > 0 ? K : 1][K > 0 ? K : 1];
-    for (int i = 0, ii = 0; i < N; ++i) {
-        if (i == i0) continue;
-        for (int j = 0, jj = 0; j < N; ++j) {
-            if (j == j0) continue;
-            S[ii][jj++] = Mz[rows[i] * N + j];
-        }
-        ++ii;
-    }
-    double2 det = make_double2(((i0 + j0) & 1) ? -1.0 : 1.0, 0.0);
-    for (int k = 0; k < K; ++k) {
-        int p = k;
-        double best = abs2(S[k][k]);
-        for (int i = k + 1; i < K; ++i)
-            if (abs2(S[i][k]) > best) {
-                best = abs2(S[i][k]);
-                p = i;
+    if constexpr (K == 0) {
+        return make_double2(1.0, 0.0);
+    } else {
+        double2 S[K][K];
+        for (int i = 0, ii = 0; i < N; ++i) {
+            if (i == i0) continue;
+            for (int j = 0, jj = 0; j < N; ++j) {
+                if (j == j0) continue;
+                S[ii][jj++] = Mz[rows[i] * N + j];
             }
-        if (best == 0.0) return make_double2(0.0, 0.0);
-        if (p != k) {
-            det = make_double2(-det.x, -det.y);
-            for (int j = 0; j < K; ++j) {
-                const double2 t = S[k][j];
-                S[k][j] = S[p][j];
-                S[p][j] = t;
+            ++ii;
+        }
+        double2 det = make_double2(((i0 + j0) & 1) ? -1.0 : 1.0, 0.0);
+        for (int k = 0; k < K; ++k) {
+            int p = k;
+            double best = abs2(S[k][k]);
+            for (int i = k + 1; i < K; ++i)
+                if (abs2(S[i][k]) > best) {
+                    best = abs2(S[i][k]);
+                    p = i;
+                }
+            if (best == 0.0) return make_double2(0.0, 0.0);
+            if (p != k) {
+                det = make_double2(-det.x, -det.y);
+                for (int j = 0; j < K; ++j) {
+                    const double2 t = S[k][j];
+                    S[k][j] = S[p][j];
+                    S[p][j] = t;
+                }
+            }
+            det = cm2(det, S[k][k]);
+            const double ib = 1.0 / best;
+            const double2 ip = make_double2(S[k][k].x * ib, -S[k][k].y * ib);
+            for (int i = k + 1; i < K; ++i) {
+                const double2 l = cm2(S[i][k], ip);
+                for (int j = k + 1; j < K; ++j) S[i][j] = cfms(S[i][j], l, S[k][j]);
             }
         }
-        det = cm2(det, S[k][k]);
-        const double ib = 1.0 / best;
-        const double2 ip = make_double2(S[k][k].x * ib, -S[k][k].y * ib);
-        for (int i = k + 1; i < K; ++i) {
-            const double2 l = cm2(S[i][k], ip);
-            for (int j = k + 1; j < K; ++j) S[i][j] = cfms(S[i][j], l, S[k][j]);
-        }
+        return det;
     }
-    return det;
 }
 
 template <int ETA>

@@ -14,6 +14,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from _support import likely_bitstrings
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +40,11 @@ def run_exact(lib, c, bits, precision, want_err=False, **kw):
     return res, st
 
 
+def _shallow26():
+    c = W.uneven_batch64(7)[6][0]
+    return c, likely_bitstrings(c, 200, 9)
+
+
 SMALL = [
     ("brick8_exact", lambda: W.brick8_exact()),
     ("brick-after", lambda: (W.brick_circuit(8, 4, 3, seed=0, cphase_between=False), W.sector_bitstrings_all(8, 4))),
@@ -53,6 +59,10 @@ SMALL = [
                                                 seed=8), W.spin_sector_bitstrings_all(5, 2, 2))),
     ("lucj-20q-uneven", lambda: (W.lucj_circuit(10, 4, 2, 1, n_onsite=5, n_same=3, angle_sampler=W.normal_var(0.3),
                                                 seed=9), W.spin_sector_bitstrings(10, 4, 2, 517, np.random.default_rng(4)))),
+    # 26 modes, 7+7 particles, one brick layer: the last rows of every branch
+    # matrix are exactly zero, so the exchange form's coefficients carry FP64
+    # rounding noise where the exact values vanish (tiny FP32 pivots)
+    ("shallow-26q-zero-rows", lambda: _shallow26()),
 ]
 
 

@@ -18,6 +18,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from _support import likely_bitstrings
 
 pytestmark = pytest.mark.gpu
 
@@ -42,37 +43,15 @@ def _shifted(c, n_modes, offset):
     return W.Circuit(n_modes, W.modes_to_bits([m + offset for m in c.occupied_modes()]), g)
 
 
-def _likely(c, nb, seed, pool=400):
-    """nb bitstrings that carry probability: the most probable (by the oracle) of
-    a pool of one- and two-particle moves away from the initial occupation."""
-    rng = np.random.default_rng(seed)
-    occ0 = c.occupied_modes()
-    cand = set()
-    for _ in range(20 * pool):
-        if len(cand) >= pool:
-            break
-        occ = set(occ0)
-        for _ in range(int(rng.integers(1, 4))):  # hop particles by at most 4 modes
-            m = int(rng.choice(sorted(occ)))
-            t = m + int(rng.integers(-4, 5))
-            if 0 <= t < c.n_modes and t not in occ:
-                occ.remove(m)
-                occ.add(t)
-        cand.add(tuple(sorted(occ)))
-    bits = np.array([W.modes_to_bits(m) for m in sorted(cand)], dtype=np.uint64)
-    p = O.exact_probabilities(c, bits)
-    return bits[np.argsort(-p)[:nb]]
-
-
 def _n128():
     # a 16-mode circuit placed on modes 56..71, across the two bitstring words
     c = _shifted(W.random_fig4_circuit(16, 4, 4, 3, seed=41), 128, 56)
-    return c, _likely(c, 24, 5)
+    return c, likely_bitstrings(c, 24, 5)
 
 
 def _big_eta(n, eta, k, seed, nb):
     c = W.random_fig4_circuit(n, eta, k, 2, seed=seed)
-    return c, _likely(c, nb, 5)
+    return c, likely_bitstrings(c, nb, 5)
 
 
 CASES = [
