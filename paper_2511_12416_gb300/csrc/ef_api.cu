@@ -58,7 +58,8 @@ struct CP {
     double theta, c, s, pT0, pT1, ratio0, ratio1;
     uint32_t T;
     int blk_p, blk_q;  // active block of each mode (-1 = none)
-    int cls;           // -1 free, 0/1 local to block, 2 shared
+    int cls;           // -1 outside the Exact enumeration, 0/1 local to block, 2 shared
+    bool phase_only;   // changes no probability (see the gate classes in prepare)
 };
 
 // A device buffer that only grows.
@@ -286,13 +287,33 @@ int prepare(ef_circuit* c) {
         c->blk[b].n = (int)c->blk[b].modes.size();
         c->blk[b].eta = (int)c->blk[b].cols.size();
     }
+    // Controlled-phase gates that change no probability: each of their modes is
+    // untouched by Givens rotations either before the gate (it still holds its
+    // initial occupation, so the gate reduces to a phase on the other mode or to
+    // a global phase) or after it (the gate, or that reduced phase, commutes with
+    // everything later and ends as a diagonal gate before the measurement). Their
+    // factor c + i s sigma in the amplitude (sigma = +-1, the sign their flips give
+    // the minors) has modulus 1, so the Exact path leaves them out of its branch
+    // enumeration (class -1 below) and their probability gradient is zero. The
+    // Raw Estimate keeps them: its estimator samples every gate.
+    std::vector<int> first_rot(n, (int)c->gates.size()), last_rot(n, -1);
+    for (int gi = 0; gi < (int)c->gates.size(); ++gi) {
+        const ef_gate& g = c->gates[gi];
+        if (g.kind != EF_GIVENS) continue;
+        for (int m : {g.p, g.q}) {
+            first_rot[m] = std::min(first_rot[m], gi);
+            last_rot[m] = std::max(last_rot[m], gi);
+        }
+    }
     // gate classes
     c->shared_gates.clear();
     for (int j = 0; j < k; ++j) {
         CP& cp = c->cps[j];
         cp.blk_p = block_of[cp.p];
         cp.blk_q = block_of[cp.q];
-        if (cp.blk_p < 0 && cp.blk_q < 0) cp.cls = -1;
+        auto settled = [&](int m) { return first_rot[m] > cp.gate || last_rot[m] < cp.gate; };
+        cp.phase_only = settled(cp.p) && settled(cp.q);
+        if ((cp.blk_p < 0 && cp.blk_q < 0) || cp.phase_only) cp.cls = -1;
         else if (cp.blk_p >= 0 && cp.blk_q >= 0 && cp.blk_p != cp.blk_q) cp.cls = 2;
         else cp.cls = cp.blk_p >= 0 ? cp.blk_p : cp.blk_q;
         if (cp.cls == 2) c->shared_gates.push_back(j);

@@ -60,9 +60,9 @@ __device__ __forceinline__ double min_pivot2(double) { return 2.2250738585072014
 __device__ __forceinline__ float inv_u2(float) { return 281474976710656.0f; }
 __device__ __forceinline__ double inv_u2(double) { return 81129638414606681695789005144064.0; }
 // One pivot's term (k+1) c_k^2 / |u_kk|^2 of the error proxy er2 (units of
-// u^2), raised to 1/u^2 (relative error 1) once it exceeds 1/(16 u^2).
+// u^2), raised to 1/u^2 (relative error 1) once it exceeds 1/(256 u^2).
 template <typename R> __device__ __forceinline__ R pivot_err_term(R t) {
-    return t > R(0.0625) * inv_u2(R(0)) ? fmax(t, inv_u2(R(0))) : t;
+    return t > R(1.0 / 256) * inv_u2(R(0)) ? fmax(t, inv_u2(R(0))) : t;
 }
 
 // multiply by i^ph (ph in 0..3)
@@ -170,10 +170,11 @@ __device__ __forceinline__ int nth_row(uint64_t w0, uint64_t w1, uint64_t m0, ui
 // er2 = sum_k (k+1) c_k^2 / |u_kk|^2 (in units of u^2). A zero pivot (|u_kk|^2
 // below the smallest normal number) leaves det ~ 0 with an absolute error of about
 // sqrt(k+1) u c_k prod_{j != k} |u_jj|; zabs2 is the square of that (0 when no
-// pivot vanished). A pivot whose own term puts its relative error above 1/4 is
-// rounding noise (the minor is singular up to rounding, and the accumulated
-// error of such a pivot was seen up to ~4x its term): its term becomes 1/u^2,
-// a relative error of 1 for the determinant. The elimination steps are a
+// pivot vanished). A pivot whose own term puts its relative error above 1/16 is
+// taken for rounding noise (the minor is singular up to rounding; the backward
+// error of the elimination allows such a pivot up to ~n * growth * u * c_k,
+// several times its term, and one of a singular 7x7 minor sat at 0.27): its
+// term becomes 1/u^2, a relative error of 1 for the determinant. The elimination steps are a
 // compile-time recursion so every matrix index is a constant and the matrix
 // stays in registers.
 // Rows K+1.. minus l_i times the pivot row K, l_i = A[i][K] / pivot (ip = 1/pivot).
