@@ -1,4 +1,6 @@
 """Helpers shared by the GPU parity tests (no fixtures)."""
+import math
+
 import numpy as np
 
 import oracle as O
@@ -26,3 +28,26 @@ def likely_bitstrings(c, nb, seed, pool=400):
     bits = np.array([W.modes_to_bits(m) for m in sorted(cand)], dtype=np.uint64)
     p = O.exact_probabilities(c, bits)
     return bits[np.argsort(-p)[:nb]]
+
+
+def neutral_gates_circuit():
+    """8 modes, modes 0-3 occupied: two controlled-phase gates before any
+    rotation, one on modes 3, 4 after two brick layers (with a third to
+    follow), one after the last rotation. Returns the circuit and the angle
+    slots of the first, second and fourth gate (probability-neutral) and of
+    the third."""
+    rng = np.random.default_rng(31)
+    recs = [(W.CPHASE, 0, 5, 0.7, 0.0), (W.CPHASE, 3, 4, -0.9, 0.0)]
+    def bricks():
+        for start in (0, 1):
+            for p in range(start, 7, 2):
+                recs.append((W.GIVENS, p, p + 1, *rng.uniform(0, 2 * math.pi, 2)))
+    bricks()
+    bricks()
+    recs.append((W.CPHASE, 3, 4, 1.1, 0.0))
+    bricks()
+    recs.append((W.CPHASE, 1, 6, 0.5, 0.0))
+    c = W.Circuit(8, W.modes_to_bits([0, 1, 2, 3]), W.make_gates(recs))
+    lay = O.angle_layout(c.gates)
+    cp = [s for s, (gi, _) in enumerate(lay) if int(c.gates[gi]["kind"]) == W.CPHASE]
+    return c, [cp[0], cp[1], cp[3]], cp[2]

@@ -14,7 +14,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from _support import likely_bitstrings
+from _support import likely_bitstrings, neutral_gates_circuit
 
 pytestmark = pytest.mark.gpu
 
@@ -189,3 +189,16 @@ def test_exact_repeatable_and_device_api(lib):
         assert np.array_equal(lib.ef_prob_exact(h, bits), p_host)
     finally:
         lib.ef_circuit_destroy(h)
+
+
+def test_exact_leaves_probability_neutral_gates_out(lib):
+    """Of the circuit's four controlled-phase gates only the one between
+    rotation layers can change a probability: the FP64 path factors 2 minors
+    per bitstring (one flip bit), not 2^4, and still matches the oracle, which
+    enumerates every gate."""
+    c, _, _ = neutral_gates_circuit()
+    bits = W.sector_bitstrings_all(8, 4)
+    p, st = run_exact(lib, c, bits, lib.EF_PREC_FP64)
+    assert np.max(rel_err(p, O.exact_probabilities(c, bits), 1e-6 / sector_size(c))) <= 1e-10
+    assert st["executed_minor_lus"] == 2 * len(bits)
+    assert st["logical_branch_dets"] == len(bits) * 2 ** 4

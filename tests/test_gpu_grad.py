@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from _support import neutral_gates_circuit
 
 pytestmark = pytest.mark.gpu
 
@@ -129,3 +130,20 @@ def test_autograd_function(lib):
         assert np.max(np.abs(ang.grad.numpy() - g_ref)) <= 1e-9 * max(1.0, np.max(np.abs(g_ref)))
     finally:
         lib.ef_circuit_destroy(h)
+
+
+
+def test_grad_with_probability_neutral_gates(lib):
+    """The Exact path leaves controlled-phase gates that no rotation touches
+    before or after out of its enumeration (each multiplies every amplitude by
+    a unit-modulus factor). The adjoint must still match the oracle, which keeps
+    every gate, with a zero gradient for those gates' angles."""
+    c, neutral, active = neutral_gates_circuit()
+    bits = W.sector_bitstrings_all(8, 4)
+    g = np.random.default_rng(8).uniform(-1, 1, len(bits))
+    p, grad = gpu_grad(lib, c, bits, g)
+    ref = O.prob_gradient(c, bits, g)
+    assert np.max(np.abs(grad - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(p - O.exact_probabilities(c, bits))) < 1e-12
+    assert abs(ref[active]) > 1e-3 and abs(grad[active]) > 1e-3
+    assert np.all(np.abs(ref[neutral]) < 1e-12) and np.all(np.abs(grad[neutral]) < 1e-12)
