@@ -963,7 +963,7 @@ void exact_account(ef_circuit* c, int64_t nb) {
 
 int exact_enqueue_build(ef_circuit* c, const ExactBuffers& eb, cudaStream_t s, ef::LaunchStats& st) {
     const bool fp64_only = c->opt.precision == EF_PREC_FP64;
-    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_build_branches(eb.blk[b], !fp64_only, s, st));
+    if (c->nblocks > 0) EF_CK(ef::launch_build_branches(eb.blk[0], eb.blk[1], c->nblocks, !fp64_only, s, st));
     return EF_OK;
 }
 
@@ -1344,7 +1344,7 @@ int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_
     EF_CK(c->dPbar.ensure((size_t)nb * ((size_t)1 << ksh) * sizeof(double2)));
     EF_CK(c->dSumP.ensure(((size_t)1 << ksh) * sizeof(double2)));
     g.pbar = c->dPbar.as<double2>();
-    for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_build_branches(g.blk[b], false, s, st));
+    if (c->nblocks > 0) EF_CK(ef::launch_build_branches(g.blk[0], g.blk[1], c->nblocks, false, s, st));
     for (int b = 0; b < c->nblocks; ++b) EF_CK(ef::launch_exact_lu_f64(g.blk[b], d_bits, nb, nullptr, nullptr, nb, s, st));
     if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
     EF_CK(ef::launch_grad(g, d_bits, nb, d_grad_p, d_out_p, s, st));

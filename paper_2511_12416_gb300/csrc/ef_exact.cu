@@ -31,8 +31,11 @@ namespace ef {
 
 // ---------------------------------------------------------------- 1. builder
 
-__global__ void __launch_bounds__(128) k_build_branches(ExactBlockDev B, int want32) {
+// Blocks B0 and B1 (blockIdx.y) in one launch: each is mostly latency at this
+// size, so two launches cost about twice one.
+__global__ void __launch_bounds__(128) k_build_branches(ExactBlockDev B0, ExactBlockDev B1, int want32) {
     extern __shared__ double2 smb[];
+    const ExactBlockDev& B = blockIdx.y ? B1 : B0;
     const int n = B.n, eta = B.eta, ne = n * eta;
     double2* bufA = smb;
     double2* bufB = smb + ne;
@@ -77,13 +80,20 @@ __global__ void __launch_bounds__(128) k_build_branches(ExactBlockDev B, int wan
     }
 }
 
-cudaError_t launch_build_branches(const ExactBlockDev& b, bool want32, cudaStream_t s, LaunchStats& st) {
-    const size_t smem = (size_t)2 * b.n * b.eta * sizeof(double2) + (size_t)b.n * sizeof(int);
+cudaError_t launch_build_branches(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, bool want32,
+                                  cudaStream_t s, LaunchStats& st) {
+    if (nblk < 1 || nblk > 2) return cudaErrorInvalidValue;
+    size_t smem = 0;
+    uint32_t ny = 1;
+    for (int i = 0; i < nblk; ++i) {
+        const ExactBlockDev& b = i ? b1 : b0;
+        smem = std::max(smem, (size_t)2 * b.n * b.eta * sizeof(double2) + (size_t)b.n * sizeof(int));
+        ny = std::max(ny, 1u << b.r);
+    }
     cudaError_t e = cudaFuncSetAttribute(k_build_branches, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const uint32_t ny = 1u << b.r;
-    const int grid = (int)std::min<uint32_t>(ny, 152u * 16u);
-    k_build_branches<<<grid, 128, smem, s>>>(b, want32 ? 1 : 0);
+    const dim3 grid(std::min<uint32_t>(ny, 152u * 16u), (unsigned)nblk);
+    k_build_branches<<<grid, 128, smem, s>>>(b0, nblk == 2 ? b1 : b0, want32 ? 1 : 0);
     st.launches += 1;
     return cudaGetLastError();
 }

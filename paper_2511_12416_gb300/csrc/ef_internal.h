@@ -152,7 +152,9 @@ struct LaunchStats {
     int64_t executed_lus = 0;
 };
 
-cudaError_t launch_build_branches(const ExactBlockDev& b, bool want32, cudaStream_t s, LaunchStats& st);
+// branch matrices of nblk (1 or 2) mode blocks in one launch
+cudaError_t launch_build_branches(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, bool want32,
+                                  cudaStream_t s, LaunchStats& st);
 cudaError_t launch_exact_lu_f32(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
                                 cudaStream_t s, LaunchStats& st);
 // largest pattern count (log2) a chunk of the FP32 kernel can stage in shared memory
