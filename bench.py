@@ -43,7 +43,7 @@ NB = 10_000
 # the pattern matrices are read from L2 and most of the 41 MB of FP32 determinants stay in L2
 # until the combine.
 # To be re-measured whenever that kernel changes.
-LU_DRAM_BYTES_PER_LAUNCH = 1_265_664  # mean of two launches (1.37 MB, 1.16 MB), 8-pattern chunks
+LU_DRAM_BYTES_PER_LAUNCH = None  # one launch now covers both mode blocks: to be re-measured
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 L2_BYTES = 129 * 2 ** 20
 BATCH_TRAJ = 1000  # trajectories per Raw Estimate circuit of the batch workload

@@ -970,12 +970,16 @@ int exact_enqueue_build(ef_circuit* c, const ExactBuffers& eb, cudaStream_t s, e
 int exact_enqueue_lu(ef_circuit* c, const ExactBuffers& eb, const uint64_t* bits, int64_t nbb, cudaStream_t s,
                      ef::LaunchStats& st) {
     const bool fp64_only = c->opt.precision == EF_PREC_FP64;
+    if (!fp64_only && c->nblocks == 2 && eb.blk[0].eta == eb.blk[1].eta && eb.blk[0].eta <= ef::kMaxEtaThread) {
+        EF_CK(ef::launch_exact_lu_f32(eb.blk[0], eb.blk[1], 2, bits, nbb, s, st));
+        return EF_OK;
+    }
     for (int b = 0; b < c->nblocks; ++b) {
         const ef::ExactBlockDev& d = eb.blk[b];
         if (fp64_only) {
             EF_CK(ef::launch_exact_lu_f64(d, bits, nbb, nullptr, nullptr, nbb, s, st));
         } else if (d.eta <= ef::kMaxEtaThread) {
-            EF_CK(ef::launch_exact_lu_f32(d, bits, nbb, s, st));
+            EF_CK(ef::launch_exact_lu_f32(d, d, 1, bits, nbb, s, st));
         } else {
             EF_CK(ef::launch_exact_lu_rows(d, bits, nbb, nullptr, nullptr, nbb, false, s, st));
         }

@@ -155,8 +155,9 @@ struct LaunchStats {
 // branch matrices of nblk (1 or 2) mode blocks in one launch
 cudaError_t launch_build_branches(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, bool want32,
                                   cudaStream_t s, LaunchStats& st);
-cudaError_t launch_exact_lu_f32(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
-                                cudaStream_t s, LaunchStats& st);
+// FP32 minors of nblk (1 or 2) mode blocks with the same eta in one launch
+cudaError_t launch_exact_lu_f32(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, const uint64_t* bits,
+                                int64_t nb, cudaStream_t s, LaunchStats& st);
 // largest pattern count (log2) a chunk of the FP32 kernel can stage in shared memory
 int exact_f32_chunk_log2(int n, int eta, int r, int64_t nb);
 // Persistent FP32 LU over a work queue of several circuits with the same eta:

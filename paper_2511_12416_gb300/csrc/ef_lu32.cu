@@ -29,9 +29,11 @@ int exact_f32_chunk_log2(int n, int eta, int r, int64_t nb) {
 }
 
 template <int ETA>
-__global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uint64_t* __restrict__ bits,
-                                                      int64_t nb) {
+__global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B0, ExactBlockDev B1,
+                                                      const uint64_t* __restrict__ bits, int64_t nb) {
     extern __shared__ float2 smM[];
+    // both mode blocks in one launch (blockIdx.z): one tail instead of two
+    const ExactBlockDev& B = blockIdx.z ? B1 : B0;
     constexpr int S = ETA | 1;
     const int n = B.n;
     const int Y = 1 << B.c_log2;
@@ -69,35 +71,43 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B, const uin
 }
 
 template <int ETA>
-static cudaError_t launch_f32_eta(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, cudaStream_t s) {
+static cudaError_t launch_f32_eta(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, const uint64_t* bits,
+                                  int64_t nb, cudaStream_t s) {
     constexpr int S = ETA | 1;
-    const size_t smem = (size_t)(1 << b.c_log2) * b.n * S * sizeof(float2);
+    size_t smem = 0;
+    int chunks = 1;
+    for (int i = 0; i < nblk; ++i) {
+        const ExactBlockDev& b = i ? b1 : b0;
+        smem = std::max(smem, (size_t)(1 << b.c_log2) * b.n * S * sizeof(float2));
+        chunks = std::max(chunks, b.n_chunks);
+    }
     cudaError_t e = cudaFuncSetAttribute(k_exact_lu_f32<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((nb + 127) / 128), (unsigned)std::min(b.n_chunks, 65535));
-    k_exact_lu_f32<ETA><<<grid, 128, smem, s>>>(b, bits, nb);
+    dim3 grid((unsigned)((nb + 127) / 128), (unsigned)std::min(chunks, 65535), (unsigned)nblk);
+    k_exact_lu_f32<ETA><<<grid, 128, smem, s>>>(b0, nblk == 2 ? b1 : b0, bits, nb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_exact_lu_f32(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, cudaStream_t s,
-                                LaunchStats& st) {
+cudaError_t launch_exact_lu_f32(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, const uint64_t* bits,
+                                int64_t nb, cudaStream_t s, LaunchStats& st) {
     if (nb <= 0) return cudaSuccess;
+    if (nblk < 1 || nblk > 2 || (nblk == 2 && b1.eta != b0.eta)) return cudaErrorInvalidValue;
     cudaError_t e;
-    switch (b.eta) {
-        case 1: e = launch_f32_eta<1>(b, bits, nb, s); break;
-        case 2: e = launch_f32_eta<2>(b, bits, nb, s); break;
-        case 3: e = launch_f32_eta<3>(b, bits, nb, s); break;
-        case 4: e = launch_f32_eta<4>(b, bits, nb, s); break;
-        case 5: e = launch_f32_eta<5>(b, bits, nb, s); break;
-        case 6: e = launch_f32_eta<6>(b, bits, nb, s); break;
-        case 7: e = launch_f32_eta<7>(b, bits, nb, s); break;
-        case 8: e = launch_f32_eta<8>(b, bits, nb, s); break;
-        case 9: e = launch_f32_eta<9>(b, bits, nb, s); break;
-        case 10: e = launch_f32_eta<10>(b, bits, nb, s); break;
+    switch (b0.eta) {
+        case 1: e = launch_f32_eta<1>(b0, b1, nblk, bits, nb, s); break;
+        case 2: e = launch_f32_eta<2>(b0, b1, nblk, bits, nb, s); break;
+        case 3: e = launch_f32_eta<3>(b0, b1, nblk, bits, nb, s); break;
+        case 4: e = launch_f32_eta<4>(b0, b1, nblk, bits, nb, s); break;
+        case 5: e = launch_f32_eta<5>(b0, b1, nblk, bits, nb, s); break;
+        case 6: e = launch_f32_eta<6>(b0, b1, nblk, bits, nb, s); break;
+        case 7: e = launch_f32_eta<7>(b0, b1, nblk, bits, nb, s); break;
+        case 8: e = launch_f32_eta<8>(b0, b1, nblk, bits, nb, s); break;
+        case 9: e = launch_f32_eta<9>(b0, b1, nblk, bits, nb, s); break;
+        case 10: e = launch_f32_eta<10>(b0, b1, nblk, bits, nb, s); break;
         default: return cudaErrorInvalidValue;
     }
     st.launches += 1;
-    st.executed_lus += nb * ((int64_t)1 << b.r);
+    for (int i = 0; i < nblk; ++i) st.executed_lus += nb * ((int64_t)1 << (i ? b1 : b0).r);
     return e;
 }
 
