@@ -39,11 +39,11 @@ METRIC = "Born-rule probabilities/s and branch-dets/s at rel err ≤1e-5 vs FP64
 UNIT = "probabilities/s"
 NB = 10_000
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_exact_lu_f32<8> launch on this workload
-# (ncu, GB300, launches 7-12 of `bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-fp64-form`):
-# the pattern matrices are read from L2 and most of the 41 MB of FP32 determinants stay in L2
-# until the combine.
-# To be re-measured whenever that kernel changes.
-LU_DRAM_BYTES_PER_LAUNCH = None  # one launch now covers both mode blocks: to be re-measured
+# (ncu, GB300, `-k regex:"k_exact_lu_f32|k_exact_combine_wp" -s 9 -c 6` on `bench.py --steps 3
+# --warmup 3 --no-cpu-baseline --no-fp64-form`): one launch covers both mode blocks; of the 82 MB of FP32 determinants it
+# writes, 24-27 MB reach DRAM within the launch and the rest stays in L2 until the combine; the
+# pattern matrices are read from L2. To be re-measured whenever that kernel changes.
+LU_DRAM_BYTES_PER_LAUNCH = 26_846_848  # mean of two launches (28.4 MB, 25.3 MB), 8-pattern chunks
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 L2_BYTES = 129 * 2 ** 20
 BATCH_TRAJ = 1000  # trajectories per Raw Estimate circuit of the batch workload
