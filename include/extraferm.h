@@ -156,8 +156,10 @@ int ef_circuit_set_precision(ef_circuit* c, int32_t precision, double tol);
  * relative error of the FP32-minor path (0 on the FP64 path; for results
  * redone in FP64 under EF_PREC_AUTO, the FP32 estimate that triggered it,
  * negated). nb = 0 is allowed. The circuit's 2^k trajectories are enumerated
- * per independent mode block; k per block is limited by device memory
- * (EF_EUNSUPPORTED beyond 2^24 sub-branches per block). */
+ * per independent mode block as distinct flip patterns; controlled-phase
+ * gates whose modes no Givens rotation touches before them, or after them,
+ * change no probability and are left out. k per block is limited by device
+ * memory (EF_EUNSUPPORTED beyond 2^24 sub-branches per block). */
 int ef_prob_exact(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, double* err_out);
 int ef_prob_exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out,
                       double* d_err_out, void* stream);
