@@ -1012,6 +1012,14 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
     float2* A32 = reinterpret_cast<float2*>(G + n0 + n1);
     float2* Q = A32;
     float* V = reinterpret_cast<float*>(G);
+    // G, Q and V hold pattern z = (h, l) of block B at offset (B ? n0 : 0) +
+    // (l << sh_B) + h (h the row, l the local bits): the NL values of a lane's
+    // row then lie rows apart, and a warp's accesses to one l are consecutive
+    // (with z as the index they were 2^RL apart: 32-way bank conflicts).
+    const int sh0 = C.r[0] - RL, sh1 = C.r[1] - RL;
+    const auto phys = [&](int B, uint32_t z) -> int {
+        return (int)(((z & (uint32_t)(NL - 1)) << (B ? sh1 : sh0)) | (z >> RL));
+    };
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t pos = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; pos < count; pos += nwarps) {
         const int64_t b = list ? (int64_t)list[pos] : pos;
@@ -1050,9 +1058,10 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
 #pragma unroll
             for (int l = 0; l < NL; ++l) v[l] = cf_mul(v[l], Wh[l]);
             row_wht<RL>(v, cf_add, cf_sub);
-            float4* GB = G + (B ? n0 : 0) + z0;
+            float4* GB = G + (B ? n0 : 0) + (B ? row - rows0 : row);
+            const int shB = B ? sh1 : sh0;
 #pragma unroll
-            for (int l = 0; l < NL; ++l) GB[l] = v[l];
+            for (int l = 0; l < NL; ++l) GB[l << shB] = v[l];
         }
         __syncwarp();
         // 2. amp = sum_xs WS(xs) F_0(s_0(xs)) F_1(s_1(xs)); with one-to-one s_B,
@@ -1064,13 +1073,13 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
         }
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int xs = lane; xs < nsh; xs += 32) {
-            const uint32_t z0 = C.s[0][xs], z1 = C.s[1][xs];
-            const float4 a0 = G[z0], a1 = G[n0 + z1];
+            const int p0 = phys(0, C.s[0][xs]), p1 = n0 + phys(1, C.s[1][xs]);
+            const float4 a0 = G[p0], a1 = G[p1];
             const float4 w = C.WSDF[xs];
             if (scatter) {
                 const float2 w32 = make_float2(w.x, w.z);
-                Q[z0] = cmul(w32, make_float2(a1.x, a1.z));
-                Q[n0 + z1] = cmul(w32, make_float2(a0.x, a0.z));
+                Q[p0] = cmul(w32, make_float2(a1.x, a1.z));
+                Q[p1] = cmul(w32, make_float2(a0.x, a0.z));
             } else if (want_err) {
                 A32[xs] = make_float2(a0.x, a0.z);
                 A32[nsh + xs] = make_float2(a1.x, a1.z);
@@ -1088,13 +1097,15 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
                 if (row >= rows) break;
                 const int B = row < rows0 ? 0 : 1;
                 const int z0 = (B ? row - rows0 : row) << RL;
+                // this row's entries in Q and V: NL values 1 << sh_B apart
+                const int pb = (B ? n0 : 0) + (B ? row - rows0 : row), shB = B ? sh1 : sh0;
                 const float2* Aoth = A32 + (1 - B) * nsh;
                 float2 q[NL];
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
                     q[l] = make_float2(0.f, 0.f);
                     if (scatter) {
-                        q[l] = Q[(B ? n0 : 0) + (z0 | l)];
+                        q[l] = Q[pb + (l << shB)];
                         continue;
                     }
                     for (uint32_t g = C.inv_off[B][z0 | l]; g < C.inv_off[B][(z0 | l) + 1]; ++g) {
@@ -1115,7 +1126,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
                 for (int l = 0; l < NL; ++l) {
                     const float vt = fmaf(q[l].x, q[l].x, q[l].y * q[l].y) * errt[rr][l];
                     var += vt;
-                    if (emit) V[(B ? n0 : 0) + (z0 | l)] = vt;
+                    if (emit) V[pb + (l << shB)] = vt;
                 }
             }
         }
@@ -1166,10 +1177,12 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
                 else hi = mid;
             }
             const float t = __uint_as_float(lo);
-            for (int z = lane; z < n0 + n1; z += 32)
-                if (!(V[z] <= t)) {
-                    const int B = z < n0 ? 0 : 1;
-                    C.mlist[B][atomicAdd(&C.mcount[B], 1)] = make_int2((int)pos, B ? z - n0 : z);
+            for (int p = lane; p < n0 + n1; p += 32)
+                if (!(V[p] <= t)) {
+                    const int B = p < n0 ? 0 : 1;
+                    const int pz = B ? p - n0 : p, shB = B ? sh1 : sh0;
+                    const int z = ((pz & ((1 << shB) - 1)) << RL) | (pz >> shB);  // back to (h, l)
+                    C.mlist[B][atomicAdd(&C.mcount[B], 1)] = make_int2((int)pos, z);
                 }
         }
         __syncwarp();
