@@ -1016,9 +1016,10 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
     // (l << sh_B) + h (h the row, l the local bits): the NL values of a lane's
     // row then lie rows apart, and a warp's accesses to one l are consecutive
     // (with z as the index they were 2^RL apart: 32-way bank conflicts).
-    const int sh0 = C.r[0] - RL, sh1 = C.r[1] - RL;
+    // (C.r[B] - RL read from the parameter space where needed: two more live
+    // registers made the kernel spill)
     const auto phys = [&](int B, uint32_t z) -> int {
-        return (int)(((z & (uint32_t)(NL - 1)) << (B ? sh1 : sh0)) | (z >> RL));
+        return (int)(((z & (uint32_t)(NL - 1)) << (C.r[B] - RL)) | (z >> RL));
     };
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t pos = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; pos < count; pos += nwarps) {
@@ -1059,7 +1060,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
             for (int l = 0; l < NL; ++l) v[l] = cf_mul(v[l], Wh[l]);
             row_wht<RL>(v, cf_add, cf_sub);
             float4* GB = G + (B ? n0 : 0) + (B ? row - rows0 : row);
-            const int shB = B ? sh1 : sh0;
+            const int shB = C.r[B] - RL;
 #pragma unroll
             for (int l = 0; l < NL; ++l) GB[l << shB] = v[l];
         }
@@ -1098,7 +1099,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
                 const int B = row < rows0 ? 0 : 1;
                 const int z0 = (B ? row - rows0 : row) << RL;
                 // this row's entries in Q and V: NL values 1 << sh_B apart
-                const int pb = (B ? n0 : 0) + (B ? row - rows0 : row), shB = B ? sh1 : sh0;
+                const int pb = (B ? n0 : 0) + (B ? row - rows0 : row), shB = C.r[B] - RL;
                 const float2* Aoth = A32 + (1 - B) * nsh;
                 float2 q[NL];
 #pragma unroll
@@ -1180,7 +1181,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
             for (int p = lane; p < n0 + n1; p += 32)
                 if (!(V[p] <= t)) {
                     const int B = p < n0 ? 0 : 1;
-                    const int pz = B ? p - n0 : p, shB = B ? sh1 : sh0;
+                    const int pz = B ? p - n0 : p, shB = C.r[B] - RL;
                     const int z = ((pz & ((1 << shB) - 1)) << RL) | (pz >> shB);  // back to (h, l)
                     C.mlist[B][atomicAdd(&C.mcount[B], 1)] = make_int2((int)pos, z);
                 }
