@@ -269,6 +269,20 @@ __device__ double2 cofactor(const double2* __restrict__ Mz, const int (&rows)[N]
     }
 }
 
+// The cofactor path for a singular minor, kept out of line: inlined next to
+// the in-place inverse it made k_grad_minors<6> spill 4.4 KB per thread. The
+// rows are passed as the bitstring's local row mask (ascending set bits), so
+// that no register array of the caller has its address taken.
+template <int N>
+__device__ __noinline__ double2 cofactor_of_mask(const double2* __restrict__ Mz, uint64_t lm, int i0, int j0) {
+    int rows[N];
+    for (int i = 0; i < N; ++i) {
+        rows[i] = __ffsll((long long)lm) - 1;
+        lm &= lm - 1;
+    }
+    return cofactor<N>(Mz, rows, i0, j0);
+}
+
 template <int ETA>
 __global__ void __launch_bounds__(128) k_grad_minors(GradDev G, int blk, const uint64_t* __restrict__ bits,
                                                      int64_t nb) {
@@ -277,8 +291,11 @@ __global__ void __launch_bounds__(128) k_grad_minors(GradDev G, int blk, const u
     const int n = B.n, L = B.L;
     const int ne = n * ETA;
     extern __shared__ double2 sm[];
-    double2* gs = sm;                                  // [NT][ETA][ETA] per-thread cotangent blocks
-    double2* ubar = gs + NT * ETA * ETA;               // [n][ETA]
+    // per-thread cotangent blocks, GS (odd) double2 apart so that a warp's
+    // stores of one (i, j) spread over every bank (ETA^2 apart: up to 16-way)
+    constexpr int GS = (ETA * ETA) | 1;
+    double2* gs = sm;                                  // [NT][GS]
+    double2* ubar = gs + NT * GS;                      // [n][ETA]
     double2* xs = ubar + ne;                           // [L+1][n][ETA] forward values X_l
     double2* xb = xs + (size_t)(L + 1) * ne;           // [n][ETA] running Xbar
     uint64_t* rmask = reinterpret_cast<uint64_t*>(xb + ne);  // [NT] local row masks
@@ -293,7 +310,7 @@ __global__ void __launch_bounds__(128) k_grad_minors(GradDev G, int blk, const u
         int rows[ETA];
         uint64_t lm = 0;
         bool ok = false;
-        double2* gt = gs + (size_t)tid * ETA * ETA;
+        double2* gt = gs + (size_t)tid * GS;
         if (b < nb) {
             ok = decode_rows<ETA>(bits[2 * b], bits[2 * b + 1], B.mask0, B.mask1, rows);
             const double2 cb = cot[b];
@@ -312,7 +329,7 @@ __global__ void __launch_bounds__(128) k_grad_minors(GradDev G, int blk, const u
                         for (int j = 0; j < ETA; ++j) gt[i * ETA + j] = cm2(f, A[j][i]);
                 } else {
                     for (int i = 0; i < ETA; ++i)
-                        for (int j = 0; j < ETA; ++j) gt[i * ETA + j] = cm2(cb, cofactor<ETA>(Mz, rows, i, j));
+                        for (int j = 0; j < ETA; ++j) gt[i * ETA + j] = cm2(cb, cofactor_of_mask<ETA>(Mz, lm, i, j));
                 }
             }
         }
@@ -329,7 +346,7 @@ __global__ void __launch_bounds__(128) k_grad_minors(GradDev G, int blk, const u
                 const uint64_t msk = rmask[t];
                 if ((msk >> m) & 1ull) {
                     const int i = __popcll(msk & below);
-                    const double2 g = gs[((size_t)t * ETA + i) * ETA + j];
+                    const double2 g = gs[(size_t)t * GS + i * ETA + j];
                     acc.x += g.x;
                     acc.y += g.y;
                 }
@@ -404,8 +421,9 @@ __global__ void __launch_bounds__(128) k_grad_minors(GradDev G, int blk, const u
 
 size_t grad_minors_smem(int n, int eta, int L) {
     const size_t ne = (size_t)n * eta;
-    return (size_t)128 * eta * eta * sizeof(double2) + ne * sizeof(double2) * (3 + L) + 128 * sizeof(uint64_t) +
-           (size_t)n * sizeof(int);
+    // matches k_grad_minors: [128][(eta^2) | 1] cotangent blocks, ubar, X_0..X_L, Xbar, row masks, signs
+    return (size_t)128 * ((eta * eta) | 1) * sizeof(double2) + ne * sizeof(double2) * (3 + L) +
+           128 * sizeof(uint64_t) + (size_t)n * sizeof(int);
 }
 
 template <int ETA>
