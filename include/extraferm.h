@@ -200,13 +200,19 @@ int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const do
  * no cudaMalloc, cudaFree or other allocating call; the caller still passes
  * the bitstrings and outputs (device pointers). The first call on a device
  * looks the array's device address up (cudaGetSymbolAddress with that device
- * current); make that first call before any stream capture. Calls whose
- * tables, branch matrices and per-bitstring partials do not fit return
- * EF_EINVAL with the largest batch that fits; split the batch. All calls
- * (on any circuit and any stream) share the array and it keeps the last
- * call's contents, so calls that overlap on the GPU race: order them on one
- * stream or synchronise between them. The circuit's stats of the call are
- * available from ef_circuit_get_stats (no kernel timing). */
+ * current); make that first call before any stream capture. The circuit's
+ * tables sit at the start of the array: a call copies them in from host
+ * memory (ordinary cudaMemcpyAsync from pageable memory) unless the previous
+ * call on this device was on the same circuit with the same angles, in which
+ * case it finds them in place and copies nothing. Calls whose tables, branch
+ * matrices and per-bitstring partials do not fit return EF_EINVAL with the
+ * largest batch that fits; split the batch. All calls (on any circuit and
+ * any stream) share the array and it keeps the last call's contents, so
+ * calls that overlap on the GPU race: order them on one stream or
+ * synchronise between them. The circuit's stats of the call are available
+ * from ef_circuit_get_stats (no kernel timing); under EF_PREC_AUTO its FP64
+ * recompute counts are read from the array, so they are valid only until
+ * the next allocation-free call on the same device. */
 int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out,
                               double* d_err_out, void* stream);
 
@@ -219,7 +225,8 @@ int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb,
  * not own the circuits; destroy it before them. */
 typedef struct ef_batch ef_batch;
 
-/* Create a batch over circuits cs[0..nc). */
+/* Create a batch over circuits cs[0..nc). A circuit may appear once
+ * (EF_EINVAL otherwise): its workspace holds one evaluation at a time. */
 int ef_batch_create(ef_circuit* const* cs, int32_t nc, ef_batch** out);
 
 /* Release a batch (waits for its work). NULL is allowed. */
@@ -232,7 +239,9 @@ int ef_batch_destroy(ef_batch* b);
  * that many trajectories (seed `seed`, global bitstring indices 0..nb[i]-1).
  * The first call with a given set of arguments plans, runs and captures the
  * work (synchronous); later calls with the same arguments replay the graph on
- * `stream` (asynchronous). Changing a circuit's angles re-plans. */
+ * `stream` (asynchronous). Changing a circuit's angles re-plans, and so does
+ * a call on one of the circuits outside the batch that had to enlarge the
+ * circuit's device workspace (the graph holds its addresses). */
 int ef_batch_prob_dev(ef_batch* b, const uint64_t* const* d_bits, const int64_t* nb, double* const* d_out,
                       const int64_t* n_traj, uint64_t seed, void* stream);
 

@@ -34,7 +34,7 @@ What it computes (the paper's definitions, written out):
   uniform per gate; the estimate is p_hat = |alpha_hat|^2 with
   alpha_hat = (1/t) sum_s w(x_s)/P(x_s) det U(x_s)[R, C].
 
-Readings where the paper is silent (listed in the design doc as well):
+Readings where the paper is silent:
 
 * Angles are wrapped to theta' in (-pi, pi] before the decomposition
   (c(theta) is 2 pi-periodic, the decomposition is not).

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <map>
@@ -62,15 +63,18 @@ struct CP {
     bool phase_only;   // changes no probability (see the gate classes in prepare)
 };
 
-// A device buffer that only grows.
+// A device buffer that only grows. Every reallocation bumps the owner's
+// workspace epoch, so that captured work holding the old address can tell.
 struct DBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    uint64_t* epoch = nullptr;
     cudaError_t ensure(size_t want) {
         if (want <= bytes) return cudaSuccess;
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
+        if (epoch) ++*epoch;
         cudaError_t e = cudaMalloc(&p, std::max<size_t>(want, 256));
         if (e == cudaSuccess) bytes = std::max<size_t>(want, 256);
         return e;
@@ -132,10 +136,13 @@ struct HostBlock {
     DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dOmegaHatFF, dSh, dPerm, dGoff, dInvOff, dInvXs, dM64, dM32, dD32, dD64, dMlist,
         dP64, dP32, dRC64, dRC32, dCols;
     DBuf dCot, dEbar, dTbar, dSbar, dSumT, dSumS, dSumE;
-    void release() {
+    template <typename F> void for_each_buf(F f) {
         for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dOmegaHatFF, &dSh, &dPerm, &dGoff, &dInvOff, &dInvXs, &dM64, &dM32, &dD32, &dD64, &dMlist, &dP64, &dP32, &dRC64,
                         &dRC32, &dCols, &dCot, &dEbar, &dTbar, &dSbar, &dSumT, &dSumS, &dSumE})
-            b->release();
+            f(*b);
+    }
+    void release() {
+        for_each_buf([](DBuf& b) { b.release(); });
     }
 };
 
@@ -188,11 +195,21 @@ struct ef_circuit {
     unsigned long long* last_recomp = nullptr;          // device counter of the last call's FP64 recomputes
     int last_mode = 0;                   // 1 exact, 2 approx
 
-    ~ef_circuit() {
-        for (int b = 0; b < ef::kMaxBlocks; ++b) blk[b].release();
+    uint64_t ws_epoch = 0;    // bumped whenever one of the circuit's device buffers is reallocated
+    uint64_t uid = 0;         // process-unique id (addresses of destroyed circuits are reused)
+    uint64_t tables_gen = 0;  // bumped by every host preprocessing (angles changed)
+
+    template <typename F> void for_each_buf(F f) {
+        for (int b = 0; b < ef::kMaxBlocks; ++b) blk[b].for_each_buf(f);
         for (DBuf* d : {&dWS, &dWS32, &dWSFF, &dList, &dListCount, &dRecomp, &dBits, &dOut, &dErr, &dGradP, &dGrad, &dPbar, &dSumP, &daT,
                         &daq, &dalayer, &damodes, &daPart, &dCounters})
-            d->release();
+            f(*d);
+    }
+    ef_circuit() {
+        for_each_buf([this](DBuf& d) { d.epoch = &ws_epoch; });
+    }
+    ~ef_circuit() {
+        for_each_buf([](DBuf& d) { d.release(); });
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (own_stream) cudaStreamDestroy(own_stream);
@@ -688,6 +705,7 @@ int prepare(ef_circuit* c) {
         c->R0 *= cp.ratio0;
     }
     c->dirty = true;
+    ++c->tables_gen;
     return EF_OK;
 }
 
@@ -1517,6 +1535,8 @@ int ef_circuit_create(int32_t n_modes, const uint64_t occupation[2], const ef_ga
     if (rc) return rc;
     ef_circuit* c = new (std::nothrow) ef_circuit();
     if (!c) return fail(EF_ENOMEM, "host allocation failed");
+    static std::atomic<uint64_t> next_uid{1};
+    c->uid = next_uid++;
     c->n = n_modes;
     c->occ[0] = occupation[0];
     c->occ[1] = occupation[1];
@@ -1746,6 +1766,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+// whose tables the scratch of each device holds: (circuit uid, table generation)
+uint64_t g_noalloc_owner[kNoAllocMaxDevices][2] = {};
 
 // Device address of the scratch on the current device (set up once per device).
 int noalloc_base(unsigned char** out) {
@@ -1788,6 +1810,9 @@ struct NoAllocTables {
     int* cols[ef::kMaxBlocks];
 };
 
+// The circuit's tables come first (their offsets depend on the circuit only,
+// so a later call on the same circuit finds them in place), then the buffers
+// sized by the call.
 size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* base, ExactBuffers& eb,
                       NoAllocTables& tb) {
     Carver cv{base};
@@ -1795,7 +1820,6 @@ size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* bas
     for (int b = 0; b < c->nblocks; ++b) {
         HostBlock& B = c->blk[b];
         const size_t nn = (size_t)B.n * B.n;
-        const size_t ny = (size_t)1 << B.r;
         const size_t ne = (size_t)B.n * B.eta;
         ef::ExactBlockDev& d = eb.blk[b];
         d = ef::ExactBlockDev{};
@@ -1814,14 +1838,20 @@ size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* bas
         eb.goff[b] = cv.take<uint32_t>(B.goff.size());
         eb.inv_off[b] = cv.take<uint32_t>(B.inv_off.size());
         eb.inv_xs[b] = cv.take<uint32_t>(B.inv_xs.size());
+    }
+    eb.WS = cv.take<double2>(c->WS.size());
+    eb.WS32 = cv.take<float2>(c->WS32.size());
+    eb.WSFF = cv.take<float4>(c->WS.size());
+    for (int b = 0; b < c->nblocks; ++b) {
+        HostBlock& B = c->blk[b];
+        const size_t ny = (size_t)1 << B.r;
+        const size_t ne = (size_t)B.n * B.eta;
+        ef::ExactBlockDev& d = eb.blk[b];
         d.M64 = cv.take<double2>(ny * ne);
         d.M32 = want32 ? cv.take<float2>(ny * ne) : nullptr;
         d.D32 = c->opt.precision != EF_PREC_FP64 ? cv.take<float4>(ny * (size_t)eb.cap) : nullptr;
         d.D64 = c->opt.precision != EF_PREC_FP32_MINOR ? cv.take<double2>(ny * (size_t)eb.cap) : nullptr;
     }
-    eb.WS = cv.take<double2>(c->WS.size());
-    eb.WS32 = cv.take<float2>(c->WS32.size());
-    eb.WSFF = cv.take<float4>(c->WS.size());
     eb.list = cv.take<int>((size_t)eb.cap);
     eb.list2 = cv.take<int>((size_t)eb.cap);
     eb.count = cv.take<int>(4);
@@ -1881,8 +1911,19 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
     c->stats.logical_branch_dets = nb * (int64_t)std::ldexp(1.0, (int)c->cps.size());
     if (nb == 0) return EF_OK;
 
+    // the tables are copied in unless this circuit, with these angles, was the
+    // scratch's last user on this device
+    int dev = 0;
+    EF_CK(cudaGetDevice(&dev));
+    bool have_tables;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        have_tables = g_noalloc_owner[dev][0] == c->uid && g_noalloc_owner[dev][1] == c->tables_gen;
+        g_noalloc_owner[dev][0] = c->uid;
+        g_noalloc_owner[dev][1] = c->tables_gen;
+    }
     ef::LaunchStats st;
-    for (int b = 0; b < c->nblocks; ++b) {
+    for (int b = 0; b < c->nblocks && !have_tables; ++b) {
         HostBlock& B = c->blk[b];
         const size_t nn = (size_t)B.n * B.n;
         const ef::ExactBlockDev& d = eb.blk[b];
@@ -1903,10 +1944,17 @@ extern "C" int ef_prob_exact_noalloc_dev(ef_circuit* c, const uint64_t* d_bits, 
         EF_CK(cudaGetLastError());
         st.launches += 1;
     }
-    EF_CK(copy_in_c(eb.WS, c->WS.data(), c->WS.size(), s));
-    EF_CK(copy_in(eb.WS32, c->WS32, s));
-    EF_CK(copy_in(eb.WSFF, c->WSFF, s));
-    return run_exact(c, eb, d_bits, nb, d_out, d_err_out, s, st);
+    if (!have_tables) {
+        EF_CK(copy_in_c(eb.WS, c->WS.data(), c->WS.size(), s));
+        EF_CK(copy_in(eb.WS32, c->WS32, s));
+        EF_CK(copy_in(eb.WSFF, c->WSFF, s));
+    }
+    const int rc2 = run_exact(c, eb, d_bits, nb, d_out, d_err_out, s, st);
+    if (rc2) {  // the tables may be partly written: copy them again next time
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        g_noalloc_owner[dev][0] = 0;
+    }
+    return rc2;
 }
 
 // =================================================================== multi-circuit batch
@@ -2106,8 +2154,15 @@ extern "C" int ef_batch_create(ef_circuit* const* cs, int32_t nc, ef_batch** out
     if (!out) return fail(EF_EINVAL, "out is NULL");
     *out = nullptr;
     if (nc <= 0 || !cs) return fail(EF_EINVAL, "a batch needs at least one circuit");
-    for (int i = 0; i < nc; ++i)
+    for (int i = 0; i < nc; ++i) {
         if (!cs[i]) return fail(EF_EINVAL, "NULL circuit in batch");
+        // a circuit's workspace holds one call's branch matrices, determinants
+        // and partial sums, so two entries of one circuit would overwrite each other
+        for (int j = 0; j < i; ++j)
+            if (cs[j] == cs[i])
+                return fail(EF_EINVAL, "circuit " + std::to_string(i) + " appears twice in the batch (entry " +
+                                           std::to_string(j) + "); create a second circuit for it");
+    }
     ef_batch* bt = new (std::nothrow) ef_batch();
     if (!bt) return fail(EF_ENOMEM, "host allocation failed");
     bt->cs.assign(cs, cs + nc);
@@ -2154,7 +2209,11 @@ extern "C" int ef_batch_prob_dev(ef_batch* bt, const uint64_t* const* d_bits, co
                                (uint64_t)n_traj[i], (uint64_t)bt->cs[i]->opt.precision});
         dirty = dirty || bt->cs[i]->dirty;
     }
-    if (bt->exec && key == bt->key && !dirty) {
+    // the graph holds addresses of the circuits' workspaces: a call outside the
+    // batch that regrew one of them (its epoch moved) forces a new plan
+    std::vector<uint64_t> key_now = key;
+    for (int i = 0; i < nc; ++i) key_now.push_back(bt->cs[i]->ws_epoch);
+    if (bt->exec && key_now == bt->key && !dirty) {
         EF_CK(cudaGraphLaunch(bt->exec, s));
         return EF_OK;
     }
@@ -2259,6 +2318,7 @@ extern "C" int ef_batch_prob_dev(ef_batch* bt, const uint64_t* const* d_bits, co
     if (e != cudaSuccess) return fail(EF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     bt->graph = g;
     EF_CK(cudaGraphInstantiate(&bt->exec, bt->graph, 0));
+    for (int i = 0; i < nc; ++i) key.push_back(bt->cs[i]->ws_epoch);
     bt->key = key;
     return EF_OK;
 }

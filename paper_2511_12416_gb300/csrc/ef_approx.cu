@@ -250,7 +250,7 @@ static cudaError_t launch_approx_eta(const ApproxDev& a, const uint64_t* bits, i
     size_t smem = ((size_t)((a.k + 3) & ~3) * sizeof(uint32_t) + 15) & ~(size_t)15;
     for (int B = 0; B < a.nblocks; ++B)
         smem += (size_t)ETA * ETA * sizeof(cplx_t<R>) + (size_t)a.blk[B].L * ETA * a.blk[B].n * sizeof(cplx_t<R>);
-    cudaError_t e = cudaFuncSetAttribute(k_approx<R, ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dynamic_smem((const void*)k_approx<R, ETA>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)nb, (unsigned)a.n_chunks);
     k_approx<R, ETA><<<grid, 128, smem, s>>>(a, bits, nb);

@@ -23,11 +23,40 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "ef_common.cuh"
 #include "ef_internal.h"
 
 namespace ef {
+
+cudaError_t raise_dynamic_smem(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[{dev, kernel}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
+int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (cached[dev] <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
 
 // ---------------------------------------------------------------- 1. builder
 
@@ -90,9 +119,9 @@ cudaError_t launch_build_branches(const ExactBlockDev& b0, const ExactBlockDev& 
         smem = std::max(smem, (size_t)2 * b.n * b.eta * sizeof(double2) + (size_t)b.n * sizeof(int));
         ny = std::max(ny, 1u << b.r);
     }
-    cudaError_t e = cudaFuncSetAttribute(k_build_branches, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dynamic_smem((const void*)k_build_branches, smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid(std::min<uint32_t>(ny, 152u * 16u), (unsigned)nblk);
+    const dim3 grid(std::min<uint32_t>(ny, (uint32_t)sm_count() * 16u), (unsigned)nblk);
     k_build_branches<<<grid, 128, smem, s>>>(b0, nblk == 2 ? b1 : b0, want32 ? 1 : 0);
     st.launches += 1;
     return cudaGetLastError();
@@ -174,7 +203,7 @@ template <int ETA>
 static cudaError_t launch_f64m_eta(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, const uint64_t* bits,
                                    const int2* mlist0, const int2* mlist1, const int* mcount, int64_t stride,
                                    cudaStream_t s) {
-    k_exact_lu_f64m<ETA><<<152 * 8, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride);
+    k_exact_lu_f64m<ETA><<<sm_count() * 8, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride);
     return cudaGetLastError();
 }
 
@@ -203,7 +232,7 @@ static cudaError_t launch_f64t_eta(const ExactBlockDev& b, const uint64_t* bits,
                                    const int* list_count, int64_t stride, cudaStream_t s) {
     // list mode: the list is usually short or empty, so a small grid strides over it
     const int64_t items = (list ? stride : nb) << b.r;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, list ? 152 * 4 : 152 * 32));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, list ? sm_count() * 4 : sm_count() * 32));
     k_exact_lu_f64t<ETA><<<(unsigned)blocks, 128, 0, s>>>(b, bits, nb, list, list_count, stride);
     return cudaGetLastError();
 }
@@ -267,7 +296,7 @@ static cudaError_t launch_rows_g(const ExactBlockDev& b, const uint64_t* bits, i
     const int64_t items = (list ? stride : nb) * (int64_t)b.n_chunks;
     const int64_t warps = (items + (32 / G) - 1) / (32 / G);
     int64_t blocks = (warps + 7) / 8;
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 16));
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 16));
     k_exact_lu_rows<R, G><<<(unsigned)blocks, 256, 0, s>>>(b, bits, nb, list, list_count, stride,
                                                           reinterpret_cast<const cplx_t<R>*>(M));
     return cudaGetLastError();
@@ -1206,10 +1235,9 @@ static cudaError_t launch_wp_r(const ExactCombineDev& c, size_t per_warp, const 
                                int64_t stride, const int* list, const int* list_count, double* out, double* err,
                                int* append_list, int* append_count, cudaStream_t s) {
     const size_t smem = 4 * per_warp;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_exact_combine_wp<RL, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dynamic_smem((const void*)k_exact_combine_wp<RL, RPL>, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nb + 3) / 4, 152 * 8));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nb + 3) / 4, (int64_t)sm_count() * 8));
     k_exact_combine_wp<RL, RPL><<<(unsigned)blocks, 128, smem, s>>>(c, bits, nb, stride, list, list_count, out, err,
                                                                     append_list, append_count);
     return cudaGetLastError();
@@ -1256,19 +1284,18 @@ cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits,
                              (size_t)4 * ((size_t)1 << c.k_sh) +
                              (c.mlist[0] ? ((size_t)1 << c.r[0]) + ((size_t)1 << c.r[1]) : 0);
         const size_t smem = 2 * words * sizeof(float);
-        cudaError_t e = cudaFuncSetAttribute(k_exact_combine_ffr<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = raise_dynamic_smem((const void*)k_exact_combine_ffr<NT>, smem);
         if (e != cudaSuccess) return e;
-        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, 152 * 12));
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * 12));
         k_exact_combine_ffr<NT><<<(unsigned)blocks, NT, smem, s>>>(c, bits, nb, stride, list, list_count, out, err,
                                                                    append_list, append_count);
         st.launches += 1;
         return cudaGetLastError();
     }
     const size_t smem = exact_combine_smem(c);
-    cudaError_t e = cudaFuncSetAttribute(k_exact_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dynamic_smem((const void*)k_exact_combine, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, 152 * 16));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * 16));
     k_exact_combine<<<(unsigned)blocks, 256, smem, s>>>(c, bits, nb, stride, list, list_count, out, err, append_list,
                                                         append_count);
     st.launches += 1;

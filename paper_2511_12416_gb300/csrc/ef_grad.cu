@@ -431,7 +431,7 @@ static cudaError_t launch_grad_minors_eta(const GradDev& g, int blk, const uint6
                                           cudaStream_t s) {
     const ExactBlockDev& B = g.blk[blk];
     const size_t smem = grad_minors_smem(B.n, ETA, B.L);
-    cudaError_t e = cudaFuncSetAttribute(k_grad_minors<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dynamic_smem((const void*)k_grad_minors<ETA>, smem);
     if (e != cudaSuccess) return e;
     k_grad_minors<ETA><<<1u << B.r, 128, smem, s>>>(g, blk, bits, nb);
     return cudaGetLastError();
@@ -441,9 +441,9 @@ cudaError_t launch_grad(const GradDev& g, const uint64_t* bits, int64_t nb, cons
                         cudaStream_t s, LaunchStats& st) {
     if (nb <= 0) return cudaSuccess;
     const size_t smem = (size_t)2 * ((size_t)1 << g.cm.k_sh) * sizeof(double2);
-    cudaError_t e = cudaFuncSetAttribute(k_grad_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dynamic_smem((const void*)k_grad_combine, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, 152 * 16));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * 16));
     k_grad_combine<<<(unsigned)blocks, 256, smem, s>>>(g, bits, nb, grad_p, out_p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     st.launches += 1;

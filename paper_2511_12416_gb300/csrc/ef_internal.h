@@ -152,6 +152,17 @@ struct LaunchStats {
     int64_t executed_lus = 0;
 };
 
+// Streaming multiprocessors of the current device (queried once per device;
+// grids are sized in multiples of it).
+int sm_count();
+
+// Raise the kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`; it is never lowered. The limit is a property of the kernel,
+// not of a launch: lowering it for a small launch would invalidate a larger
+// launch of the same kernel recorded earlier in a CUDA graph (a replay that
+// re-checks each node against the current limit then fails that node).
+cudaError_t raise_dynamic_smem(const void* kernel, size_t bytes);
+
 // branch matrices of nblk (1 or 2) mode blocks in one launch
 cudaError_t launch_build_branches(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, bool want32,
                                   cudaStream_t s, LaunchStats& st);

@@ -24,7 +24,7 @@ int exact_f32_chunk_log2(int n, int eta, int r, int64_t nb) {
     // keep at least ~5 waves of 3 CTAs per SM (measured on the 32-qubit workload:
     // 8 patterns per chunk beat 4 by 2 % and 16 lose 5 %)
     const int64_t tiles = (nb + 127) / 128;
-    while (cl > 0 && tiles * ((int64_t)1 << (r - cl)) < 152 * 3 * 5) --cl;
+    while (cl > 0 && tiles * ((int64_t)1 << (r - cl)) < (int64_t)sm_count() * 3 * 5) --cl;
     return cl;
 }
 
@@ -81,7 +81,7 @@ static cudaError_t launch_f32_eta(const ExactBlockDev& b0, const ExactBlockDev& 
         smem = std::max(smem, (size_t)(1 << b.c_log2) * b.n * S * sizeof(float2));
         chunks = std::max(chunks, b.n_chunks);
     }
-    cudaError_t e = cudaFuncSetAttribute(k_exact_lu_f32<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dynamic_smem((const void*)k_exact_lu_f32<ETA>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((nb + 127) / 128), (unsigned)std::min(chunks, 65535), (unsigned)nblk);
     k_exact_lu_f32<ETA><<<grid, 128, smem, s>>>(b0, nblk == 2 ? b1 : b0, bits, nb);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restri
 template <int ETA>
 static cudaError_t launch_queue_eta(const QueueEntry* q, int nq, int64_t n_items, unsigned long long* head,
                                     size_t smem, int grid, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_queue_lu_f32<ETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dynamic_smem((const void*)k_queue_lu_f32<ETA>, smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) {  // one wave of resident CTAs
         int dev = 0, sms = 0, occ = 0;

@@ -115,3 +115,56 @@ def test_batch_uneven64_subset(lib):
         lib.ef_batch_destroy(b)
         for h in hs:
             lib.ef_circuit_destroy(h)
+
+
+def test_batch_rejects_a_circuit_listed_twice(lib):
+    c, _ = W.brick8_exact()
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates)
+    try:
+        with pytest.raises(lib.ExtraFermError) as e:
+            lib.ef_batch_create([h, h])
+        assert e.value.status == lib.EF_EINVAL
+    finally:
+        lib.ef_circuit_destroy(h)
+
+
+def test_batch_replans_after_a_direct_call_regrows_a_workspace(lib):
+    """The captured graph holds the circuits' workspace addresses. A direct
+    call with many more bitstrings reallocates circuit 0's determinant
+    buffers; the next batch call must re-plan (not replay stale addresses)
+    and still give the circuits' own results."""
+    rng = np.random.default_rng(4)
+    items = [(W.lucj_circuit(6, 3, 3, 1, n_onsite=6, n_same=3, angle_sampler=W.normal_var(0.1), seed=7),
+              W.spin_sector_bitstrings_all(6, 3, 3)[:40], 0),
+             (W.random_fig4_circuit(10, 4, 7, 3, seed=31, angle_std=1.2), W.sector_bitstrings_all(10, 4)[:30], 300)]
+    hs = [lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_AUTO) for c, _, _ in items]
+    b = lib.ef_batch_create(hs)
+    try:
+        dbits = [_dev(bits) for _, bits, _ in items]
+        outs = [torch.zeros(len(bits), dtype=torch.float64, device="cuda") for _, bits, _ in items]
+        nb = [len(bits) for _, bits, _ in items]
+        traj = [t for _, _, t in items]
+        stream = torch.cuda.current_stream()
+
+        def run():
+            for o in outs:
+                o.fill_(-1.0)
+            lib.ef_batch_prob_dev(b, [d.data_ptr() for d in dbits], nb, [o.data_ptr() for o in outs], traj, 9,
+                                  stream.cuda_stream)
+            stream.synchronize()
+            return [o.cpu().numpy() for o in outs]
+
+        first = run()
+        again = run()  # replay
+        many = W.spin_sector_bitstrings(6, 3, 3, 20_000, rng)
+        lib.ef_prob_exact(hs[0], many)  # regrows circuit 0's workspace
+        lib.ef_prob_approx(hs[1], W.sector_bitstrings(10, 4, 5_000, rng), 50)  # and circuit 1's partial sums
+        after = run()
+        refs = [lib.ef_prob_exact(hs[0], items[0][1]), lib.ef_prob_approx(hs[1], items[1][1], 300, seed=9)[0]]
+        for i in range(2):
+            assert np.array_equal(first[i], refs[i]) and np.array_equal(again[i], refs[i])
+            assert np.array_equal(after[i], refs[i])
+    finally:
+        lib.ef_batch_destroy(b)
+        for h in hs:
+            lib.ef_circuit_destroy(h)

@@ -60,6 +60,35 @@ def test_noalloc_matches_allocating_entry_point_twice(lib, name, maker, prec, to
         lib.ef_circuit_destroy(h_ref)
 
 
+def test_noalloc_alternating_circuits(lib):
+    """Two circuits in turn on the shared array: each call after the other
+    circuit's copies its own tables in again; a repeated call on the same
+    circuit finds them in place. Every result equals the allocating entry
+    point's."""
+    cases = [CASES[0][1](), CASES[1][1]()]
+    stream = torch.cuda.current_stream()
+    hs, refs, devs = [], [], []
+    try:
+        for c, bits in cases:
+            h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_AUTO)
+            hs.append(h)
+            d_bits = torch.from_numpy(np.ascontiguousarray(bits).view(np.int64)).cuda()
+            ref = torch.empty(len(bits), dtype=torch.float64, device="cuda")
+            lib.ef_prob_exact_dev(h, d_bits.data_ptr(), len(bits), ref.data_ptr(), 0, stream.cuda_stream)
+            devs.append(d_bits)
+            refs.append(ref)
+        for i in (0, 1, 1, 0, 1):
+            out = torch.full((len(cases[i][1]),), -1.0, dtype=torch.float64, device="cuda")
+            lib.ef_prob_exact_noalloc_dev(hs[i], devs[i].data_ptr(), len(cases[i][1]), out.data_ptr(), 0,
+                                          stream.cuda_stream)
+            stream.synchronize()
+            p, p_ref = out.cpu().numpy(), refs[i].cpu().numpy()
+            assert np.max(np.abs(p - p_ref) / np.maximum(p_ref, _floor(cases[i][0]))) <= 1e-5
+    finally:
+        for h in hs:
+            lib.ef_circuit_destroy(h)
+
+
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch(lib):
     c, _ = W.lucj32_exact(0)
     nb = 200_000
