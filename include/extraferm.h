@@ -83,11 +83,12 @@ typedef struct {
 typedef enum {
     EF_PREC_FP64 = 0,       /* minors, LU and accumulation in FP64 */
     EF_PREC_FP32_MINOR = 1, /* minors and LU in FP32, branch sum in FP64 */
-    EF_PREC_AUTO = 2        /* FP32 minors; for results whose error estimate exceeds
-                               tol the determinants carrying most of the estimated
-                               error are redone in FP64, then the result is
-                               re-estimated and, if still above tol, all of its
-                               determinants are redone in FP64 (Exact only) */
+    EF_PREC_AUTO = 2        /* FP32 minors; Exact: for results whose error estimate
+                               exceeds tol the determinants carrying most of the
+                               estimated error are redone in FP64, then the result
+                               is re-estimated and, if still above tol, all of its
+                               determinants are redone in FP64; Raw Estimate: such
+                               results are recomputed in FP64 */
 } ef_precision;
 
 enum {
@@ -106,7 +107,8 @@ typedef struct {
     int64_t logical_branch_dets;  /* (bitstring, branch or trajectory) pairs the call evaluated */
     int64_t executed_minor_lus;   /* LU factorizations of minors actually run */
     int64_t fp64_recomputed;      /* EF_PREC_AUTO: flagged bitstrings, whose largest-error determinants
-                                     (or, if still above tol, all of them) were redone in FP64; the FP64
+                                     (or, if still above tol, all of them) were redone in FP64 (Exact),
+                                     or which were recomputed in FP64 (Raw Estimate); the FP64
                                      determinants are counted in executed_minor_lus */
     int64_t kernel_launches;      /* kernels this library launched in the call */
     int64_t sampled_flips;        /* Raw Estimate: number of x_j = 1 over all trajectories */
@@ -171,12 +173,22 @@ int ef_prob_exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double*
  * word is below T_j = round(p(x_j=1) 2^32) (>= 1 when sin(theta_j/4) != 0).
  * Importance weights use the quantised probabilities T_j/2^32, so the
  * amplitude estimate is unbiased. out[nb]: p_hat = |alpha_hat|^2;
- * stderr_out[nb] (nullable): 2 sqrt(Var_s[Re(conj(alpha_hat) Y_s)] / t). */
+ * stderr_out[nb] (nullable): 2 sqrt(Var_s[Re(conj(alpha_hat) Y_s)] / t).
+ * A trajectory's minor is evaluated as det A0 * det(I + K[N, N]) with A0 the
+ * bitstring's no-flip minor and K built once per bitstring in FP64 over the
+ * (layer, mode) pairs a gate can flip (Section IV-B, Eqs. 15-18); more than
+ * four flipped pairs in a block, or an ill-conditioned A0, take an eta x eta
+ * LU of the rank-one-updated minor instead.
+ * err_out[nb] (nullable): estimated relative error of p_hat, the rounding of
+ * the FP32 path against the same estimator in exact arithmetic (0 on the FP64
+ * path). Under EF_PREC_AUTO (blocks of at most 8 particles) bitstrings whose
+ * estimate exceeds tol are recomputed in FP64 with the same trajectories and
+ * their err_out is the triggering estimate, negated. */
 int ef_prob_approx(ef_circuit* c, const uint64_t* bits, int64_t nb, int64_t n_traj, uint64_t seed,
-                   uint64_t index_base, double* out, double* stderr_out);
+                   uint64_t index_base, double* out, double* stderr_out, double* err_out);
 int ef_prob_approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t n_traj,
                        uint64_t seed, uint64_t index_base, double* d_out, double* d_stderr_out,
-                       void* stream);
+                       double* d_err_out, void* stream);
 
 /* Vector-Jacobian product of the Exact probabilities: grad_angles[j] =
  * sum_b grad_p[b] * d p_b / d angle_j for every angle of the angle vector

@@ -64,8 +64,8 @@ SIGNATURES = {
     "ef_circuit_set_precision": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double]),
     "ef_prob_exact": (ctypes.c_int, [_P, _U64P, _I64, _DP, _DP]),
     "ef_prob_exact_dev": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
-    "ef_prob_approx": (ctypes.c_int, [_P, _U64P, _I64, _I64, _U64, _U64, _DP, _DP]),
-    "ef_prob_approx_dev": (ctypes.c_int, [_P, _P, _I64, _I64, _U64, _U64, _P, _P, _P]),
+    "ef_prob_approx": (ctypes.c_int, [_P, _U64P, _I64, _I64, _U64, _U64, _DP, _DP, _DP]),
+    "ef_prob_approx_dev": (ctypes.c_int, [_P, _P, _I64, _I64, _U64, _U64, _P, _P, _P, _P]),
     "ef_prob_grad": (ctypes.c_int, [_P, _U64P, _I64, _DP, _DP, _DP]),
     "ef_prob_grad_dev": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "ef_circuit_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(EfStats)]),
@@ -204,20 +204,25 @@ def ef_prob_exact_noalloc_dev(c, d_bits: int, nb: int, d_out: int, d_err: int = 
     _check(load().ef_prob_exact_noalloc_dev(c, d_bits, nb, d_out, d_err or None, stream or None))
 
 
-def ef_prob_approx(c, bits, n_traj: int, seed: int = 0, index_base: int = 0, want_stderr: bool = True):
+def ef_prob_approx(c, bits, n_traj: int, seed: int = 0, index_base: int = 0, want_stderr: bool = True,
+                   want_err: bool = False):
+    """Returns p_hat, then stderr (want_stderr) and the estimated relative
+    error of p_hat (want_err) as further arrays."""
     b = _bits_array(bits)
     nb = b.shape[0]
     out = np.zeros(nb)
     se = np.zeros(nb) if want_stderr else None
+    err = np.zeros(nb) if want_err else None
     _check(load().ef_prob_approx(c, b.ctypes.data_as(_U64P), nb, int(n_traj), int(seed), int(index_base),
-                                 _dptr(out), _dptr(se)))
-    return (out, se) if want_stderr else out
+                                 _dptr(out), _dptr(se), _dptr(err)))
+    res = (out,) + ((se,) if want_stderr else ()) + ((err,) if want_err else ())
+    return res if len(res) > 1 else out
 
 
 def ef_prob_approx_dev(c, d_bits: int, nb: int, n_traj: int, seed: int, index_base: int, d_out: int,
-                       d_stderr: int = 0, stream: int = 0):
+                       d_stderr: int = 0, stream: int = 0, d_err: int = 0):
     _check(load().ef_prob_approx_dev(c, d_bits, nb, int(n_traj), int(seed), int(index_base), d_out,
-                                     d_stderr or None, stream or None))
+                                     d_stderr or None, d_err or None, stream or None))
 
 
 def ef_prob_grad(c, bits, grad_p):

@@ -132,13 +132,14 @@ struct HostBlock {
     // Raw Estimate
     std::vector<cd> P;   // tri(L) x n x n
     std::vector<cd> RC;  // L x n x eta
+    std::vector<int> pair_lm;  // flippable (layer, mode) pairs, layer-major: layer << 8 | local mode
     // device
     DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dOmegaHatFF, dSh, dPerm, dGoff, dInvOff, dInvXs, dM64, dM32, dD32, dD64, dMlist,
-        dP64, dP32, dRC64, dRC32, dCols;
+        dP64, dP32, dRC64, dRC32, dCols, dPairLM;
     DBuf dCot, dEbar, dTbar, dSbar, dSumT, dSumS, dSumE;
     template <typename F> void for_each_buf(F f) {
         for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dOmegaHatFF, &dSh, &dPerm, &dGoff, &dInvOff, &dInvXs, &dM64, &dM32, &dD32, &dD64, &dMlist, &dP64, &dP32, &dRC64,
-                        &dRC32, &dCols, &dCot, &dEbar, &dTbar, &dSbar, &dSumT, &dSumS, &dSumE})
+                        &dRC32, &dCols, &dPairLM, &dCot, &dEbar, &dTbar, &dSbar, &dSumT, &dSumS, &dSumE})
             f(*b);
     }
     void release() {
@@ -177,13 +178,16 @@ struct ef_circuit {
     // Raw Estimate gate tables
     std::vector<uint32_t> aT;
     std::vector<double> aq;
+    std::vector<float> aq32;
     std::vector<uint8_t> alayer;
     std::vector<uint64_t> amodes;
+    std::vector<uint64_t> agpair;  // [kMaxBlocks][k]: flippable pairs each gate flips (K form)
+    bool kform_ok = false;         // every block has at most 64 flippable pairs
     double R0 = 1.0;
 
     bool dirty = true;
     DBuf dWS, dWS32, dWSFF, dList, dListCount, dRecomp, dBits, dOut, dErr, dGradP, dGrad, dPbar, dSumP;
-    DBuf daT, daq, dalayer, damodes, daPart, dCounters;
+    DBuf daT, daq, daq32, dalayer, damodes, dagpair, daPart, dCounters, daList;
     cudaStream_t own_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
@@ -202,7 +206,7 @@ struct ef_circuit {
     template <typename F> void for_each_buf(F f) {
         for (int b = 0; b < ef::kMaxBlocks; ++b) blk[b].for_each_buf(f);
         for (DBuf* d : {&dWS, &dWS32, &dWSFF, &dList, &dListCount, &dRecomp, &dBits, &dOut, &dErr, &dGradP, &dGrad, &dPbar, &dSumP, &daT,
-                        &daq, &dalayer, &damodes, &daPart, &dCounters})
+                        &daq, &daq32, &dalayer, &damodes, &dagpair, &daPart, &dCounters, &daList})
             f(*d);
     }
     ef_circuit() {
@@ -344,6 +348,8 @@ int prepare(ef_circuit* c) {
     double log_sector = 0.0;
     c->alayer.assign((size_t)ef::kMaxBlocks * k, 0);
     c->amodes.assign((size_t)ef::kMaxBlocks * k, 0);
+    c->agpair.assign((size_t)ef::kMaxBlocks * k, 0);
+    c->kform_ok = true;
 
     // per-block segments, layers and tables
     for (int b = 0; b < c->nblocks; ++b) {
@@ -673,6 +679,37 @@ int prepare(ef_circuit* c) {
             c->alayer[(size_t)b * k + jj] = (uint8_t)((cp.blk_p == b || cp.blk_q == b) ? layer_of_cp[jj] : 0);
             c->amodes[(size_t)b * k + jj] = (nb_ <= 64) ? mm : 0;
         }
+        // Raw Estimate K form: the (layer, mode) pairs some gate can flip, layer-major
+        B.pair_lm.clear();
+        if (nb_ <= 64) {
+            std::vector<std::vector<int>> pidx(L + 1, std::vector<int>(nb_, -1));
+            for (int l = 1; l <= L; ++l) {
+                uint64_t any = 0;
+                for (int jj = 0; jj < k; ++jj)
+                    if (c->alayer[(size_t)b * k + jj] == l) any |= c->amodes[(size_t)b * k + jj];
+                for (int m = 0; m < nb_; ++m)
+                    if ((any >> m) & 1ull) {
+                        pidx[l][m] = (int)B.pair_lm.size();
+                        B.pair_lm.push_back((l << 8) | m);
+                    }
+            }
+            if (B.pair_lm.size() > 64) {
+                c->kform_ok = false;
+            } else {
+                for (int jj = 0; jj < k; ++jj) {
+                    const int l = c->alayer[(size_t)b * k + jj];
+                    uint64_t mm = c->amodes[(size_t)b * k + jj], g = 0;
+                    while (l && mm) {
+                        const int m = __builtin_ctzll(mm);
+                        mm &= mm - 1;
+                        g ^= 1ull << pidx[l][m];
+                    }
+                    c->agpair[(size_t)b * k + jj] = g;
+                }
+            }
+        } else {
+            c->kform_ok = false;
+        }
     }
     // shared weight table: w_sh(x_sh) = i^|x_sh| prod_j (x_j ? s_j : c_j)
     c->WS.clear();
@@ -697,11 +734,13 @@ int prepare(ef_circuit* c) {
     // approx gate tables
     c->aT.assign(k, 0);
     c->aq.assign(k, 0.0);
+    c->aq32.assign(k, 0.f);
     c->R0 = 1.0;
     for (int jj = 0; jj < k; ++jj) {
         const CP& cp = c->cps[jj];
         c->aT[jj] = cp.T;
         c->aq[jj] = cp.ratio0 != 0.0 ? cp.ratio1 / cp.ratio0 : 0.0;
+        c->aq32[jj] = (float)c->aq[jj];
         c->R0 *= cp.ratio0;
     }
     c->dirty = true;
@@ -747,6 +786,7 @@ int upload_tables(ef_circuit* c, cudaStream_t s) {
         EF_CK(upload(B.dRC64, to_d2(B.RC), s));
         EF_CK(upload(B.dRC32, RC32, s));
         EF_CK(upload(B.dCols, B.cols, s));
+        EF_CK(upload(B.dPairLM, B.pair_lm, s));
     }
     EF_CK(upload(c->dWS, to_d2(c->WS), s));
     EF_CK(upload(c->dWS32, c->WS32, s));
@@ -755,8 +795,10 @@ int upload_tables(ef_circuit* c, cudaStream_t s) {
     std::copy(c->aT.begin(), c->aT.end(), T4.begin());
     EF_CK(upload(c->daT, T4, s));
     EF_CK(upload(c->daq, c->aq, s));
+    EF_CK(upload(c->daq32, c->aq32, s));
     EF_CK(upload(c->dalayer, c->alayer, s));
     EF_CK(upload(c->damodes, c->amodes, s));
+    EF_CK(upload(c->dagpair, c->agpair, s));
     c->dirty = false;
     return EF_OK;
 }
@@ -1402,22 +1444,43 @@ int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_
 }
 
 // Buffers and launch parameters of a Raw Estimate call (no stream work).
+// Items are (bitstring, chunk of trajectories): one chunk per bitstring when
+// the bitstrings alone fill the GPU, more otherwise; CTAs stride over them.
+// The K form is used when every block has at most 64 flippable pairs and the
+// CTA's shared memory fits; otherwise every flipped minor takes the rank-one
+// form.
+ef::ApproxDev approx_dev_for(const ef_circuit* c, const ef::ApproxDev& base, bool fp64) {
+    ef::ApproxDev a = base;
+    for (int b = 0; b < c->nblocks; ++b) {
+        const HostBlock& B = c->blk[b];
+        a.blk[b].P = fp64 ? B.dP64.p : B.dP32.p;
+        a.blk[b].RC = fp64 ? B.dRC64.p : B.dRC32.p;
+    }
+    a.kform = c->kform_ok ? 1 : 0;
+    const int eta_t = ef::approx_eta_template(a);
+    if (a.kform && ef::approx_smem_bytes(a, eta_t, fp64) > (size_t)200 * 1024) a.kform = 0;
+    a.err_coef = fp64 ? 0.0 : base.err_coef;
+    return a;
+}
+
 int approx_setup(ef_circuit* c, int64_t nb, int64_t t, uint64_t seed, uint64_t base, ef::ApproxDev& a) {
     if (!c->approx_ok) return fail(EF_EUNSUPPORTED, c->approx_why);
-    if (c->opt.precision == EF_PREC_FP64)
+    const bool fp64 = c->opt.precision == EF_PREC_FP64;
+    if (fp64)
         for (int b = 0; b < c->nblocks; ++b)
             if (c->blk[b].eta > ef::kMaxApproxEta64)
                 return fail(EF_EUNSUPPORTED, "Raw Estimate with FP64 minors: at most 8 particles per mode block");
     if (t <= 0 || t > (int64_t)4294967296ll) return fail(EF_EINVAL, "n_traj must be in 1..2^32");
     if (nb > 2147483647ll) return fail(EF_EUNSUPPORTED, "Raw Estimate: more than 2^31-1 bitstrings per call");
-    const bool fp64 = c->opt.precision == EF_PREC_FP64;
     a = ef::ApproxDev{};
     a.nblocks = c->nblocks;
     a.k = (int)c->cps.size();
     a.T = c->daT.as<uint32_t>();
     a.qratio = c->daq.as<double>();
+    a.qratio32 = c->daq32.as<float>();
     a.glayer = c->dalayer.as<uint8_t>();
     a.gmodes = c->damodes.as<uint64_t>();
+    a.gpair = c->dagpair.as<uint64_t>();
     a.R0 = c->R0;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
@@ -1425,15 +1488,26 @@ int approx_setup(ef_circuit* c, int64_t nb, int64_t t, uint64_t seed, uint64_t b
     a.inactive0 = c->inactive[0];
     a.inactive1 = c->inactive[1];
     a.t = t;
-    a.traj_per_cta = 128 * 16;
+    a.nb = nb;
+    // enough (bitstring, chunk) items for about four waves of three CTAs per SM
+    const int64_t sms = ef::sm_count();
+    const int64_t target = sms * 3 * 4;
+    int64_t chunks = std::max<int64_t>(1, (target + std::max<int64_t>(nb, 1) - 1) / std::max<int64_t>(nb, 1));
+    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, t / 256));
+    int64_t per = (t + chunks - 1) / chunks;
+    per = (per + 127) / 128 * 128;
+    a.traj_per_cta = (int)std::min<int64_t>(per, (int64_t)1 << 30);
     a.n_chunks = (int)((t + a.traj_per_cta - 1) / a.traj_per_cta);
-    if (a.n_chunks > 65535) {
-        a.traj_per_cta = (int)((t + 65534) / 65535);
-        a.traj_per_cta = (a.traj_per_cta + 127) / 128 * 128;
-        a.n_chunks = (int)((t + a.traj_per_cta - 1) / a.traj_per_cta);
-    }
-    EF_CK(c->daPart.ensure((size_t)std::max<int64_t>(nb, 1) * a.n_chunks * 8 * sizeof(double)));
-    EF_CK(c->dCounters.ensure(4 * sizeof(unsigned long long)));
+    // one CTA per item (the hardware balances them); the listed FP64 redo strides
+    a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(nb, 1) * a.n_chunks, 2147483647ll));
+    a.kappa_max = 1e3;
+    // first-order rounding bounds in units of u = 2^-24, times a safety factor of 2
+    a.err_coef = 2.0 * std::ldexp(1.0, -24);
+    a.tol = c->opt.tol;
+    a.p_floor = c->p_floor;
+    EF_CK(c->daPart.ensure((size_t)std::max<int64_t>(nb, 1) * a.n_chunks * 10 * sizeof(double)));
+    EF_CK(c->dCounters.ensure(8 * sizeof(unsigned long long)));
+    EF_CK(c->daList.ensure(((size_t)std::max<int64_t>(nb, 1) + 4) * sizeof(int)));
     a.part = c->daPart.as<double>();
     a.counters = c->dCounters.as<unsigned long long>();
     for (int b = 0; b < c->nblocks; ++b) {
@@ -1443,26 +1517,45 @@ int approx_setup(ef_circuit* c, int64_t nb, int64_t t, uint64_t seed, uint64_t b
         a.blk[b].L = B.L;
         a.blk[b].mask0 = B.mask[0];
         a.blk[b].mask1 = B.mask[1];
-        a.blk[b].P = fp64 ? B.dP64.p : B.dP32.p;
-        a.blk[b].RC = fp64 ? B.dRC64.p : B.dRC32.p;
+        a.blk[b].P64 = B.dP64.as<double2>();
+        a.blk[b].RC64 = B.dRC64.as<double2>();
         a.blk[b].cols = B.dCols.as<int>();
+        a.blk[b].f = (int)B.pair_lm.size();
+        a.blk[b].pair_lm = B.dPairLM.as<int>();
+    }
+    a = approx_dev_for(c, a, fp64);
+    return EF_OK;
+}
+
+// The Raw Estimate launches: trajectories, finalisation and, under
+// EF_PREC_AUTO, the FP64 redo of the bitstrings whose estimated relative
+// error exceeds tol (same seed and global indices, so the same trajectories).
+int approx_enqueue(ef_circuit* c, const ef::ApproxDev& a, const uint64_t* d_bits, double* d_out, double* d_se,
+                   double* d_err, cudaStream_t s, ef::LaunchStats& st) {
+    const bool fp64 = c->opt.precision == EF_PREC_FP64;
+    const bool autofix = c->opt.precision == EF_PREC_AUTO && ef::approx_eta_template(a) <= ef::kMaxApproxEta64;
+    int* list = c->daList.as<int>();
+    int* list_count = list + std::max<int64_t>(a.nb, 1);
+    EF_CK(cudaMemsetAsync(a.counters, 0, 8 * sizeof(unsigned long long), s));
+    EF_CK(cudaMemsetAsync(list_count, 0, sizeof(int), s));
+    if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
+    EF_CK(ef::launch_approx(a, d_bits, fp64, s, st));
+    if (c->timed) EF_CK(cudaEventRecord(c->ev1, s));
+    EF_CK(ef::launch_approx_finalize(a, d_out, d_se, d_err, autofix ? list : nullptr, list_count, false, s, st));
+    if (autofix) {
+        ef::ApproxDev r = approx_dev_for(c, a, true);
+        r.list = list;
+        r.list_count = list_count;
+        r.counters = a.counters + 4;  // the redo's own flips, LUs and rank-one minors
+        r.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)a.grid, (int64_t)ef::sm_count() * 24));
+        EF_CK(ef::launch_approx(r, d_bits, true, s, st));
+        EF_CK(ef::launch_approx_finalize(r, d_out, d_se, d_err, nullptr, nullptr, true, s, st));
     }
     return EF_OK;
 }
 
-int approx_enqueue(ef_circuit* c, const ef::ApproxDev& a, const uint64_t* d_bits, int64_t nb, double* d_out,
-                   double* d_se, cudaStream_t s, ef::LaunchStats& st) {
-    const bool fp64 = c->opt.precision == EF_PREC_FP64;
-    EF_CK(cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned long long), s));
-    if (c->timed) EF_CK(cudaEventRecord(c->ev0, s));
-    EF_CK(ef::launch_approx(a, d_bits, nb, fp64, s, st));
-    if (c->timed) EF_CK(cudaEventRecord(c->ev1, s));
-    EF_CK(ef::launch_approx_finalize(a, nb, d_out, d_se, s, st));
-    return EF_OK;
-}
-
 int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uint64_t seed, uint64_t base,
-               double* d_out, double* d_se, cudaStream_t s) {
+               double* d_out, double* d_se, double* d_err, cudaStream_t s) {
     if (!c->approx_ok) return fail(EF_EUNSUPPORTED, c->approx_why);
     if (t <= 0 || t > (int64_t)4294967296ll) return fail(EF_EINVAL, "n_traj must be in 1..2^32");
     int rc = begin_call(c, s, 2);
@@ -1473,28 +1566,34 @@ int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uin
     rc = approx_setup(c, nb, t, seed, base, a);
     if (rc) return rc;
     ef::LaunchStats st;
-    rc = approx_enqueue(c, a, d_bits, nb, d_out, d_se, s, st);
+    rc = approx_enqueue(c, a, d_bits, d_out, d_se, d_err, s, st);
     if (rc) return rc;
     c->stats.dominant_kernel_launches = 1;
     c->stats.kernel_launches = st.launches;
     return EF_OK;
 }
 
+// Host-pointer form of a *_dev call: bitstrings in, up to three per-bitstring
+// outputs back (out2, out3 nullable), on the circuit's own stream.
 template <typename F>
-int host_call(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, double* out2, F&& dev_call) {
+int host_call(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, double* out2, double* out3,
+              F&& dev_call) {
     if (!c->own_stream) EF_CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
     cudaStream_t s = c->own_stream;
     if (nb > 0) {
         EF_CK(c->dBits.ensure((size_t)nb * 2 * sizeof(uint64_t)));
-        EF_CK(c->dOut.ensure((size_t)nb * sizeof(double)));
-        if (out2) EF_CK(c->dErr.ensure((size_t)nb * sizeof(double)));
+        EF_CK(c->dOut.ensure((size_t)nb * 3 * sizeof(double)));
         EF_CK(cudaMemcpyAsync(c->dBits.p, bits, (size_t)nb * 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     }
-    int rc = dev_call(c->dBits.as<uint64_t>(), c->dOut.as<double>(), out2 ? c->dErr.as<double>() : nullptr, s);
+    double* d0 = c->dOut.as<double>();
+    double* d2 = out2 ? d0 + nb : nullptr;
+    double* d3 = out3 ? d0 + 2 * nb : nullptr;
+    int rc = dev_call(c->dBits.as<uint64_t>(), d0, d2, d3, s);
     if (rc) return rc;
     if (nb > 0) {
-        EF_CK(cudaMemcpyAsync(out, c->dOut.p, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
-        if (out2) EF_CK(cudaMemcpyAsync(out2, c->dErr.p, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EF_CK(cudaMemcpyAsync(out, d0, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (out2) EF_CK(cudaMemcpyAsync(out2, d2, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (out3) EF_CK(cudaMemcpyAsync(out3, d3, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     EF_CK(cudaStreamSynchronize(s));
     return EF_OK;
@@ -1651,27 +1750,29 @@ int ef_prob_exact(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, 
     if (nb < 0 || (nb > 0 && (!bits || !out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
     int rc = check_bits_host(c, bits, nb);
     if (rc) return rc;
-    return host_call(c, bits, nb, out, err_out, [&](const uint64_t* db, double* dout, double* derr, cudaStream_t s) {
-        return ef_prob_exact_dev(c, db, nb, dout, derr, s);
-    });
+    return host_call(c, bits, nb, out, err_out, nullptr,
+                     [&](const uint64_t* db, double* dout, double* derr, double*, cudaStream_t s) {
+                         return ef_prob_exact_dev(c, db, nb, dout, derr, s);
+                     });
 }
 
 int ef_prob_approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t n_traj, uint64_t seed,
-                       uint64_t index_base, double* d_out, double* d_stderr_out, void* stream) {
+                       uint64_t index_base, double* d_out, double* d_stderr_out, double* d_err_out, void* stream) {
     if (!c) return fail(EF_EINVAL, "NULL circuit");
     if (nb < 0 || (nb > 0 && (!d_bits || !d_out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
-    return approx_dev(c, d_bits, nb, n_traj, seed, index_base, d_out, d_stderr_out, (cudaStream_t)stream);
+    return approx_dev(c, d_bits, nb, n_traj, seed, index_base, d_out, d_stderr_out, d_err_out, (cudaStream_t)stream);
 }
 
 int ef_prob_approx(ef_circuit* c, const uint64_t* bits, int64_t nb, int64_t n_traj, uint64_t seed,
-                   uint64_t index_base, double* out, double* stderr_out) {
+                   uint64_t index_base, double* out, double* stderr_out, double* err_out) {
     if (!c) return fail(EF_EINVAL, "NULL circuit");
     if (nb < 0 || (nb > 0 && (!bits || !out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
     int rc = check_bits_host(c, bits, nb);
     if (rc) return rc;
-    return host_call(c, bits, nb, out, stderr_out, [&](const uint64_t* db, double* dout, double* dse, cudaStream_t s) {
-        return ef_prob_approx_dev(c, db, nb, n_traj, seed, index_base, dout, dse, s);
-    });
+    return host_call(c, bits, nb, out, stderr_out, err_out,
+                     [&](const uint64_t* db, double* dout, double* dse, double* derr, cudaStream_t s) {
+                         return ef_prob_approx_dev(c, db, nb, n_traj, seed, index_base, dout, dse, derr, s);
+                     });
 }
 
 int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_grad_p, double* d_out_p,
@@ -1736,8 +1837,11 @@ int ef_circuit_get_stats(ef_circuit* c, ef_stats* st) {
     if (c->last_mode == 2 && c->dCounters.p) {
         unsigned long long h[4] = {0, 0, 0, 0};
         EF_CK(cudaMemcpy(h, c->dCounters.p, sizeof(h), cudaMemcpyDeviceToHost));
+        unsigned long long r[2] = {0, 0};
+        EF_CK(cudaMemcpy(r, c->dCounters.as<unsigned long long>() + 4, sizeof(r), cudaMemcpyDeviceToHost));
         c->stats.sampled_flips = (int64_t)h[0];
-        c->stats.executed_minor_lus = (int64_t)h[1];
+        c->stats.executed_minor_lus = (int64_t)h[1] + (int64_t)r[1];
+        c->stats.fp64_recomputed = (int64_t)h[3];
     }
     *st = c->stats;
     return EF_OK;
@@ -2062,7 +2166,7 @@ int batch_enqueue(ef_batch* bt, cudaStream_t s, ef::LaunchStats& st) {
     for (size_t i = 0; i < bt->items.size(); ++i) {
         ef_batch::Item& it = bt->items[i];
         if (it.mode != 3 || it.nb == 0) continue;
-        int rc = approx_enqueue(bt->cs[i], it.a, it.bits, it.nb, it.out, nullptr, bt->side[rr++ % ns], st);
+        int rc = approx_enqueue(bt->cs[i], it.a, it.bits, it.out, nullptr, nullptr, bt->side[rr++ % ns], st);
         if (rc) return rc;
     }
     for (size_t i = 0; i < bt->items.size(); ++i) {

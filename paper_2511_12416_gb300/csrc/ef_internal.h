@@ -98,9 +98,13 @@ struct ExactCombineDev {
 struct ApproxBlockDev {
     int n, eta, L;
     uint64_t mask0, mask1;
-    const void* P;    // interval products Pi_{a..b}, a >= b, tri index a(a+1)/2 + b, n x n each
-    const void* RC;   // L x n x eta: Pi_{l..0}[:, C] for l = 0..L-1
+    const void* P;    // interval products Pi_{a..b}, a >= b, tri index a(a+1)/2 + b, n x n each (path precision)
+    const void* RC;   // L x n x eta: Pi_{l..0}[:, C] for l = 0..L-1 (path precision)
+    const double2* P64;   // FP64 copies (prologue: A0, its inverse, K)
+    const double2* RC64;
     const int* cols;  // eta local column indices
+    int f;                // flippable (layer, mode) pairs of the block (<= 64)
+    const int* pair_lm;   // [f]: (layer 1..L) << 8 | local mode, layer-major
 };
 
 struct ApproxDev {
@@ -108,17 +112,27 @@ struct ApproxDev {
     int k;
     const uint32_t* T;       // thresholds
     const double* qratio;    // (s/pT1) / (c/pT0) per gate
+    const float* qratio32;   // the same in FP32 (FP32 path)
     const uint8_t* glayer;   // [kMaxBlocks][k]: layer 1..L in the block, 0 = not touching
     const uint64_t* gmodes;  // [kMaxBlocks][k]: local modes flipped in the block
+    const uint64_t* gpair;   // [kMaxBlocks][k]: flippable pairs flipped in the block (K form)
     double R0;               // prod_j c_j / pT0_j
     uint32_t key0, key1;
     uint64_t index_base;
     uint64_t inactive0, inactive1;
     int64_t t;
+    int64_t nb;              // bitstrings of the call
+    const int* list;         // null: every bitstring; else the listed bitstrings (FP64 redo)
+    const int* list_count;   //   their number (device)
     int traj_per_cta;
     int n_chunks;
-    double* part;                 // [nb][n_chunks][8]
-    unsigned long long* counters; // [0] flips, [1] executed LUs
+    int grid;                // CTAs (grid-stride over (bitstring, chunk) items)
+    int kform;               // 1: trajectory minors through K (every block has <= 64 flippable pairs)
+    double kappa_max;        // A0 with ||A0||_1 ||A0^-1||_1 above this takes the rank-one form
+    double err_coef;         // FP32 error bound: safety factor x u32 (0: no estimate)
+    double tol, p_floor;     // EF_PREC_AUTO threshold on the estimated relative error of p_hat
+    double* part;                 // [nb][n_chunks][10]
+    unsigned long long* counters; // [0] flips, [1] executed eta x eta LUs, [2] rank-one-form minors, [3] flagged
     ApproxBlockDev blk[kMaxBlocks];
 };
 
@@ -197,9 +211,14 @@ cudaError_t launch_grad(const GradDev& g, const uint64_t* bits, int64_t nb, cons
 size_t grad_minors_smem(int n, int eta, int L);
 cudaError_t launch_sum_rows(const double2* in, int64_t count, int64_t stride, int64_t width, double2* out,
                             cudaStream_t s, LaunchStats& st);
-cudaError_t launch_approx(const ApproxDev& a, const uint64_t* bits, int64_t nb, bool fp64,
-                          cudaStream_t s, LaunchStats& st);
-cudaError_t launch_approx_finalize(const ApproxDev& a, int64_t nb, double* out, double* stderr_out,
-                                   cudaStream_t s, LaunchStats& st);
+// Raw Estimate: dynamic shared memory of one CTA; the launch over the items
+// (all bitstrings, or a.list); the per-bitstring finalisation (listed: the
+// FP64 redo of the listed bitstrings; append_list collects flagged ones)
+size_t approx_smem_bytes(const ApproxDev& a, int eta_t, bool fp64);
+int approx_eta_template(const ApproxDev& a);
+cudaError_t launch_approx(const ApproxDev& a, const uint64_t* bits, bool fp64, cudaStream_t s, LaunchStats& st);
+cudaError_t launch_approx_finalize(const ApproxDev& a, double* out, double* stderr_out, double* err_out,
+                                   int* append_list, int* append_count, bool listed, cudaStream_t s,
+                                   LaunchStats& st);
 
 }  // namespace ef
