@@ -42,7 +42,7 @@
  * aborts; ef_last_error() gives a message for the calling thread's last
  * failure. Host-pointer calls are synchronous. The *_dev calls take device
  * pointers and a cudaStream_t (passed as void*), enqueue their work on that
- * stream and return without waiting.
+ * stream and return without waiting (except ef_prob_grad_dev, see there).
  *
  * Ownership and threading. ef_circuit_create copies the gate list; the
  * caller owns every input and output buffer. A circuit owns its device
@@ -190,9 +190,32 @@ int ef_prob_approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_
                        uint64_t seed, uint64_t index_base, double* d_out, double* d_stderr_out,
                        double* d_err_out, void* stream);
 
+/* Estimate (Section III-A): |out[i] - p_i| <= eps for every bitstring, each
+ * with failure probability at most delta (Eq. 6's guarantee), without a
+ * given bound p_max. Rounds r = 0 .. R-1 of Raw Estimate on all bitstrings
+ * (host arrays, synchronous): eps_r = max(eps, eps_0 / 2^r) with
+ * eps_0 = max(eps, 1/4) and R the first round with eps_r = eps, failure
+ * budget delta / R per round, and for each bitstring the Eq. 6 trajectory
+ * count for its own bound p_max (1 in round 0, then min(p_max, p_hat + eps_r)
+ * of the previous round), rounded up to m 2^e with 4 <= m <= 8 so that equal
+ * counts share a launch. Round r draws with seed splitmix64(seed +
+ * (r + 1) 0x9E3779B97F4A7C15) and the bitstrings' global indices
+ * index_base + i (as ef_prob_approx). out: the last round's p_hat;
+ * stderr_out, traj_out (nullable): its standard error and the total
+ * trajectories spent per bitstring. Bitstrings outside the particle sector
+ * get 0 with no trajectories. EF_EUNSUPPORTED if a round needs more than
+ * 2^32 trajectories for a bitstring. */
+int ef_prob_estimate(ef_circuit* c, const uint64_t* bits, int64_t nb, double eps, double delta,
+                     uint64_t seed, uint64_t index_base, double* out, double* stderr_out,
+                     int64_t* traj_out);
+
 /* Vector-Jacobian product of the Exact probabilities: grad_angles[j] =
  * sum_b grad_p[b] * d p_b / d angle_j for every angle of the angle vector
- * (FP64). out_p (nullable) receives the probabilities. */
+ * (FP64). out_p (nullable) receives the probabilities. The device kernels
+ * reduce the cotangents to per-segment matrices; the chain rule through the
+ * individual gates runs on the host, so ef_prob_grad_dev, unlike the other
+ * *_dev calls, waits for its stream before it returns (d_grad_angles is
+ * written by then). */
 int ef_prob_grad(ef_circuit* c, const uint64_t* bits, int64_t nb, const double* grad_p,
                  double* out_p, double* grad_angles);
 int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_grad_p,

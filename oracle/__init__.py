@@ -5,9 +5,9 @@ and ``bench.py``'s CPU-baseline and reference legs, never by the library.
 """
 from .extraferm_oracle import (  # noqa: F401
     CPHASE, GIVENS, PHASE, angle_layout, cphase_list, exact_amplitudes,
-    exact_probabilities, expected_second_moment, extent, get_angles,
+    estimate, exact_probabilities, expected_second_moment, extent, get_angles,
     prob_directional_derivative, prob_gradient, raw_estimate, sample_trajectories,
-    sampling_probability, segments_and_layers, set_angles, trajectory_count_bound,
+    sampling_probability, segments_and_layers, set_angles, splitmix64, trajectory_count_bound, trajectory_grid,
     wrap_angle,
 )
 from .philox import philox4x32_10, trajectory_uniforms  # noqa: F401

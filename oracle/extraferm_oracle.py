@@ -107,7 +107,70 @@ def trajectory_count_bound(eps: float, delta: float, p_max: float, xi: float) ->
     probability delta (the printed '= 1 - delta' read as '<= delta')."""
     num = (math.sqrt(xi) + math.sqrt(p_max)) ** 2
     den = (math.sqrt(p_max + eps) - math.sqrt(p_max)) ** 2
-    return int(math.ceil(2.0 * num / den * math.log(2.0 * math.e ** 2 / delta)))
+    return int(math.ceil(2.0 * num / den * math.log(2.0 * (math.e * math.e) / delta)))
+
+
+def trajectory_grid(t: int) -> int:
+    """Round a trajectory count up to m * 2^e with 4 <= m <= 8 (the Estimate
+    driver's rounding, so that bitstrings with equal counts can share work)."""
+    t = int(t)
+    if t <= 8:
+        return max(t, 1)
+    e = t.bit_length() - 3
+    m = -(-t // (1 << e))
+    return m << e
+
+
+def splitmix64(z: int) -> int:
+    """SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014)."""
+    mask = (1 << 64) - 1
+    z &= mask
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+    return z ^ (z >> 31)
+
+
+def estimate(circuit, bitstrings, eps: float, delta: float, seed: int, b_indices=None):
+    """Estimate (Section III-A): |p_hat - p| <= eps with failure probability at
+    most delta per bitstring, without a given p_max, by rounds of Raw Estimate
+    that start loose and tighten. The paper describes the algorithm only in
+    words (start from loose error and probability upper bounds, then call Raw
+    Estimate iteratively); the schedule read here:
+
+    * eps_0 = max(eps, 1/4), eps_r = max(eps, eps_0 / 2^r), rounds r = 0..R-1
+      with R the first round at eps_r = eps; failure budget delta / R per round
+      (union bound over the rounds);
+    * round r gives each bitstring the Eq. 6 count for its own p_max (1 at
+      first, then min(p_max, p_hat + eps_r) of the previous round), rounded up
+      by ``trajectory_grid``, fresh trajectories from seed
+      splitmix64(seed + (r + 1) * 0x9E3779B97F4A7C15), and the bitstring's
+      global index;
+    * the estimate is the last round's p_hat.
+
+    Returns (p_hat, stderr, trajectories spent per bitstring)."""
+    nb = len(bitstrings)
+    if b_indices is None:
+        b_indices = list(range(nb))
+    xi = extent(circuit.gates)
+    eps0 = max(eps, 0.25)
+    R = 1
+    while R < 64 and max(eps, eps0 / 2 ** (R - 1)) > eps:
+        R += 1
+    d_r = delta / R
+    pmax = np.ones(nb)
+    ph = np.zeros(nb)
+    se = np.zeros(nb)
+    traj = np.zeros(nb, dtype=np.int64)
+    for r in range(R):
+        eps_r = max(eps, eps0 / 2 ** r)
+        seed_r = splitmix64(seed + (r + 1) * 0x9E3779B97F4A7C15)
+        for i in range(nb):
+            t = trajectory_grid(trajectory_count_bound(eps_r, d_r, float(pmax[i]), xi))
+            p_i, se_i = raw_estimate(circuit, bitstrings[i:i + 1], t=t, seed=seed_r, b_indices=[b_indices[i]])
+            ph[i], se[i] = p_i[0], se_i[0]
+            pmax[i] = min(pmax[i], ph[i] + eps_r)
+            traj[i] += t
+    return ph, se, traj
 
 
 def sampling_probability(gates, x_bits) -> float:

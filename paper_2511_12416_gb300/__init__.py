@@ -66,6 +66,8 @@ SIGNATURES = {
     "ef_prob_exact_dev": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
     "ef_prob_approx": (ctypes.c_int, [_P, _U64P, _I64, _I64, _U64, _U64, _DP, _DP, _DP]),
     "ef_prob_approx_dev": (ctypes.c_int, [_P, _P, _I64, _I64, _U64, _U64, _P, _P, _P, _P]),
+    "ef_prob_estimate": (ctypes.c_int, [_P, _U64P, _I64, ctypes.c_double, ctypes.c_double, _U64, _U64, _DP, _DP,
+                                        ctypes.POINTER(_I64)]),
     "ef_prob_grad": (ctypes.c_int, [_P, _U64P, _I64, _DP, _DP, _DP]),
     "ef_prob_grad_dev": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "ef_circuit_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(EfStats)]),
@@ -223,6 +225,18 @@ def ef_prob_approx_dev(c, d_bits: int, nb: int, n_traj: int, seed: int, index_ba
                        d_stderr: int = 0, stream: int = 0, d_err: int = 0):
     _check(load().ef_prob_approx_dev(c, d_bits, nb, int(n_traj), int(seed), int(index_base), d_out,
                                      d_stderr or None, d_err or None, stream or None))
+
+
+def ef_prob_estimate(c, bits, eps: float, delta: float, seed: int = 0, index_base: int = 0):
+    """Estimate (eps, delta): returns (p_hat, stderr, trajectories per bitstring)."""
+    b = _bits_array(bits)
+    nb = b.shape[0]
+    out = np.zeros(nb)
+    se = np.zeros(nb)
+    traj = np.zeros(nb, dtype=np.int64)
+    _check(load().ef_prob_estimate(c, b.ctypes.data_as(_U64P), nb, float(eps), float(delta), int(seed),
+                                   int(index_base), _dptr(out), _dptr(se), traj.ctypes.data_as(ctypes.POINTER(_I64))))
+    return out, se, traj
 
 
 def ef_prob_grad(c, bits, grad_p):

@@ -1573,6 +1573,142 @@ int approx_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, int64_t t, uin
     return EF_OK;
 }
 
+// ------------------------------------------------------------------ Estimate (Section III-A)
+
+// Eq. 6: trajectories sufficient for |p_hat - p| <= eps with failure
+// probability at most delta when p <= p_max (the printed "= 1 - delta" read as
+// "<= delta"), before rounding up.
+double trajectory_bound(double eps, double delta, double pmax, double xi) {
+    const double num = std::sqrt(xi) + std::sqrt(pmax);
+    const double den = std::sqrt(pmax + eps) - std::sqrt(pmax);
+    const double e = 2.718281828459045;
+    return std::ceil(2.0 * (num * num) / (den * den) * std::log(2.0 * (e * e) / delta));
+}
+
+// Trajectory counts are rounded up to m * 2^e with 4 <= m <= 8 (at most 25 %
+// more), so that the bitstrings of a round fall into a few shared launches.
+int64_t trajectory_grid(int64_t t) {
+    if (t <= 8) return std::max<int64_t>(t, 1);
+    int len = 0;
+    while (len < 63 && (t >> len) != 0) ++len;
+    const int e = len - 3;
+    const int64_t m = (t + ((int64_t)1 << e) - 1) >> e;
+    return m << e;
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): the seed of round r is
+// splitmix64(seed + (r + 1) * 0x9E3779B97F4A7C15), so rounds draw independent trajectories.
+uint64_t splitmix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+bool bitstring_in_sector(const ef_circuit* c, uint64_t w0, uint64_t w1) {
+    if ((w0 & c->inactive[0]) || (w1 & c->inactive[1])) return false;
+    for (int b = 0; b < c->nblocks; ++b)
+        if (__builtin_popcountll(w0 & c->blk[b].mask[0]) + __builtin_popcountll(w1 & c->blk[b].mask[1]) !=
+            c->blk[b].eta)
+            return false;
+    return true;
+}
+
+// The Estimate algorithm as rounds of Raw Estimate. Round r = 0 .. R-1 runs
+// every bitstring with eps_r = max(eps, eps_0 / 2^r) (eps_0 = max(eps, 1/4),
+// R the first round with eps_r = eps), delta_r = delta / R and the Eq. 6 count
+// for its own bound p_max (1 at the start), then tightens p_max to
+// min(p_max, p_hat + eps_r); the last round's p_hat is the estimate. Every
+// round holds its guarantee with probability >= 1 - delta_r, so all of them do
+// (and the final |p_hat - p| <= eps) with probability >= 1 - delta.
+int estimate_host(ef_circuit* c, const uint64_t* bits, int64_t nb, double eps, double delta, uint64_t seed,
+                  uint64_t index_base, double* out, double* se_out, int64_t* traj_out) {
+    const double eps0 = std::max(eps, 0.25);
+    int R = 1;
+    while (R < 64 && std::max(eps, std::ldexp(eps0, -(R - 1))) > eps) ++R;
+    const double delta_r = delta / R;
+    std::vector<double> pmax(nb, 1.0), ph(nb, 0.0), se(nb, 0.0);
+    std::vector<int64_t> traj(nb, 0);
+    std::vector<char> valid(nb);
+    for (int64_t i = 0; i < nb; ++i) valid[i] = bitstring_in_sector(c, bits[2 * i], bits[2 * i + 1]);
+    if (!c->own_stream) EF_CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    const cudaStream_t s = c->own_stream;
+    DBuf dbits, didx, dout;
+    EF_CK(dbits.ensure((size_t)std::max<int64_t>(nb, 1) * 2 * sizeof(uint64_t)));
+    EF_CK(didx.ensure((size_t)std::max<int64_t>(nb, 1) * sizeof(uint64_t)));
+    EF_CK(dout.ensure((size_t)std::max<int64_t>(nb, 1) * 2 * sizeof(double)));
+    ef_stats total{};
+    std::vector<uint64_t> gb, gi;
+    std::vector<double> gp, gs;
+    for (int r = 0; r < R; ++r) {
+        const double eps_r = std::max(eps, std::ldexp(eps0, -r));
+        const uint64_t seed_r = splitmix64(seed + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull);
+        std::map<int64_t, std::vector<int64_t>> groups;
+        for (int64_t i = 0; i < nb; ++i) {
+            if (!valid[i]) continue;
+            const double tb = trajectory_bound(eps_r, delta_r, pmax[i], c->xi);
+            if (!(tb <= 4294967296.0))
+                return fail(EF_EUNSUPPORTED, "ef_prob_estimate: round " + std::to_string(r) + " needs more than 2^32 "
+                                             "trajectories for bitstring " + std::to_string(i));
+            groups[trajectory_grid((int64_t)tb)].push_back(i);
+        }
+        for (auto& kv : groups) {
+            const int64_t t = std::min<int64_t>(kv.first, (int64_t)4294967296ll);
+            const std::vector<int64_t>& ids = kv.second;
+            const int64_t ng = (int64_t)ids.size();
+            gb.resize(2 * ng);
+            gi.resize(ng);
+            for (int64_t j = 0; j < ng; ++j) {
+                gb[2 * j] = bits[2 * ids[j]];
+                gb[2 * j + 1] = bits[2 * ids[j] + 1];
+                gi[j] = index_base + (uint64_t)ids[j];
+            }
+            EF_CK(cudaMemcpyAsync(dbits.p, gb.data(), gb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+            EF_CK(cudaMemcpyAsync(didx.p, gi.data(), gi.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+            int rc = begin_call(c, s, 2);
+            if (rc) return rc;
+            ef::ApproxDev a;
+            rc = approx_setup(c, ng, t, seed_r, 0, a);
+            if (rc) return rc;
+            a.gidx = didx.as<uint64_t>();
+            ef::LaunchStats st;
+            double* d_p = dout.as<double>();
+            rc = approx_enqueue(c, a, dbits.as<uint64_t>(), d_p, d_p + ng, nullptr, s, st);
+            if (rc) return rc;
+            gp.resize(ng);
+            gs.resize(ng);
+            EF_CK(cudaMemcpyAsync(gp.data(), d_p, ng * sizeof(double), cudaMemcpyDeviceToHost, s));
+            EF_CK(cudaMemcpyAsync(gs.data(), d_p + ng, ng * sizeof(double), cudaMemcpyDeviceToHost, s));
+            unsigned long long h[8] = {};
+            EF_CK(cudaMemcpyAsync(h, a.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+            EF_CK(cudaStreamSynchronize(s));
+            for (int64_t j = 0; j < ng; ++j) {
+                const int64_t i = ids[j];
+                ph[i] = gp[j];
+                se[i] = gs[j];
+                pmax[i] = std::min(pmax[i], gp[j] + eps_r);
+                traj[i] += t;
+            }
+            total.logical_branch_dets += ng * t;
+            total.sampled_flips += (int64_t)h[0];
+            total.executed_minor_lus += (int64_t)(h[1] + h[5]);
+            total.fp64_recomputed += (int64_t)h[3];
+            total.kernel_launches += st.launches;
+        }
+    }
+    for (int64_t i = 0; i < nb; ++i) {
+        out[i] = ph[i];
+        if (se_out) se_out[i] = se[i];
+        if (traj_out) traj_out[i] = traj[i];
+    }
+    cudaStreamSynchronize(s);
+    dbits.release();
+    didx.release();
+    dout.release();
+    c->stats = total;
+    c->last_mode = 0;
+    return EF_OK;
+}
+
 // Host-pointer form of a *_dev call: bitstrings in, up to three per-bitstring
 // outputs back (out2, out3 nullable), on the circuit's own stream.
 template <typename F>
@@ -1773,6 +1909,18 @@ int ef_prob_approx(ef_circuit* c, const uint64_t* bits, int64_t nb, int64_t n_tr
                      [&](const uint64_t* db, double* dout, double* dse, double* derr, cudaStream_t s) {
                          return ef_prob_approx_dev(c, db, nb, n_traj, seed, index_base, dout, dse, derr, s);
                      });
+}
+
+int ef_prob_estimate(ef_circuit* c, const uint64_t* bits, int64_t nb, double eps, double delta, uint64_t seed,
+                     uint64_t index_base, double* out, double* stderr_out, int64_t* traj_out) {
+    if (!c) return fail(EF_EINVAL, "NULL circuit");
+    if (nb < 0 || (nb > 0 && (!bits || !out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
+    if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) return fail(EF_EINVAL, "need eps > 0 and 0 < delta < 1");
+    if (!c->approx_ok) return fail(EF_EUNSUPPORTED, c->approx_why);
+    int rc = check_bits_host(c, bits, nb);
+    if (rc) return rc;
+    if (nb == 0) return EF_OK;
+    return estimate_host(c, bits, nb, eps, delta, seed, index_base, out, stderr_out, traj_out);
 }
 
 int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_grad_p, double* d_out_p,

@@ -460,8 +460,9 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
             y0r = nr;
         }
 
-        const uint32_t blo = (uint32_t)(A.index_base + (uint64_t)b);
-        const uint32_t bhi = (uint32_t)((A.index_base + (uint64_t)b) >> 32);
+        const uint64_t gi = A.gidx ? A.gidx[b] : A.index_base + (uint64_t)b;
+        const uint32_t blo = (uint32_t)gi;
+        const uint32_t bhi = (uint32_t)(gi >> 32);
         const int64_t s_begin = (int64_t)chunk * A.traj_per_cta;
         const int64_t s_end = min(A.t, s_begin + (int64_t)A.traj_per_cta);
         // Shifted sums of D_s = Y_s - y0 (y0 = the no-flip term). FP64 path,

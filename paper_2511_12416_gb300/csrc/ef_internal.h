@@ -119,6 +119,7 @@ struct ApproxDev {
     double R0;               // prod_j c_j / pT0_j
     uint32_t key0, key1;
     uint64_t index_base;
+    const uint64_t* gidx;    // null: bitstring i has global index index_base + i; else gidx[i]
     uint64_t inactive0, inactive1;
     int64_t t;
     int64_t nb;              // bitstrings of the call

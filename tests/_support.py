@@ -51,3 +51,26 @@ def neutral_gates_circuit():
     lay = O.angle_layout(c.gates)
     cp = [s for s, (gi, _) in enumerate(lay) if int(c.gates[gi]["kind"]) == W.CPHASE]
     return c, [cp[0], cp[1], cp[3]], cp[2]
+
+
+def mixed_settled_circuit():
+    """8 modes, modes 0-3 occupied. A controlled phase on modes 0 and 7 sits
+    after every rotation that touches mode 7 and before every rotation that
+    touches mode 0: mode 0 is settled before the gate and mode 7 after it, so
+    the gate changes no probability. A second controlled phase (on modes 3, 4,
+    between rotations of both) does. Returns the circuit and the angle slots
+    of the two gates (neutral, active)."""
+    rng = np.random.default_rng(41)
+    recs = []
+    for start in (1, 2, 1, 2):  # rotations on modes 1..7, none on mode 0
+        for p in range(start, 7, 2):
+            recs.append((W.GIVENS, p, p + 1, *rng.uniform(0, 2 * math.pi, 2)))
+    recs.append((W.CPHASE, 0, 7, 1.3, 0.0))
+    recs.append((W.CPHASE, 3, 4, -0.8, 0.0))
+    for start in (0, 1, 0):  # rotations on modes 0..6, none on mode 7
+        for p in range(start, 6, 2):
+            recs.append((W.GIVENS, p, p + 1, *rng.uniform(0, 2 * math.pi, 2)))
+    c = W.Circuit(8, W.modes_to_bits([0, 1, 2, 3]), W.make_gates(recs))
+    lay = O.angle_layout(c.gates)
+    cp = [s for s, (gi, _) in enumerate(lay) if int(c.gates[gi]["kind"]) == W.CPHASE]
+    return c, cp[0], cp[1]

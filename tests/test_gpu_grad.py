@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from _support import neutral_gates_circuit
+from _support import mixed_settled_circuit, neutral_gates_circuit
 
 pytestmark = pytest.mark.gpu
 
@@ -147,3 +147,55 @@ def test_grad_with_probability_neutral_gates(lib):
     assert np.max(np.abs(p - O.exact_probabilities(c, bits))) < 1e-12
     assert abs(ref[active]) > 1e-3 and abs(grad[active]) > 1e-3
     assert np.all(np.abs(ref[neutral]) < 1e-12) and np.all(np.abs(grad[neutral]) < 1e-12)
+
+
+def test_mixed_settled_gate_exact_and_gradient(lib):
+    """A controlled phase whose one mode is untouched by rotations before it and
+    whose other mode is untouched after it is left out of the Exact enumeration;
+    probabilities (FP64 and EF_PREC_AUTO) and the adjoint still match the
+    oracle, which keeps it, and its angle's gradient is zero."""
+    c, neutral, active = mixed_settled_circuit()
+    bits = W.sector_bitstrings_all(8, 4)
+    p_ref = O.exact_probabilities(c, bits)
+    floor = 1e-6 / 70
+    for prec, tol in ((lib.EF_PREC_FP64, 1e-10), (lib.EF_PREC_AUTO, 1e-5)):
+        h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=prec)
+        try:
+            p = lib.ef_prob_exact(h, bits)
+        finally:
+            lib.ef_circuit_destroy(h)
+        assert np.max(np.abs(p - p_ref) / np.maximum(p_ref, floor)) <= tol
+    g = np.random.default_rng(9).uniform(-1, 1, len(bits))
+    _, grad = gpu_grad(lib, c, bits, g)
+    ref = O.prob_gradient(c, bits, g)
+    assert np.max(np.abs(grad - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+    assert abs(ref[neutral]) < 1e-12 and abs(grad[neutral]) < 1e-12
+    assert abs(ref[active]) > 1e-4
+
+
+def _oracle_dirderiv_chunk(args):
+    c, bits, g, v = args
+    return O.prob_directional_derivative(c, bits, g, v)
+
+
+def test_grad_lucj40_grad_all_bitstrings_directional_against_oracle(lib):
+    """The 40-qubit LUCJ gradient workload on all 4096 bitstrings: the adjoint
+    along one random direction against the oracle's forward-mode derivative of
+    L = sum_b w_b log p_b (oracle work split over host cores)."""
+    import multiprocessing as mp
+    import os
+    c, bits, w = W.lucj40_grad()
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_FP64)
+    try:
+        p = lib.ef_prob_exact(h, bits)
+        _, grad = lib.ef_prob_grad(h, bits, w / p)
+    finally:
+        lib.ef_circuit_destroy(h)
+    v = np.random.default_rng(21).normal(size=len(grad))
+    g = w / p
+    ncores = max(1, min(32, len(os.sched_getaffinity(0))))
+    chunks = [(c, bits[i::ncores], g[i::ncores], v) for i in range(ncores)]
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        dref = float(sum(pool.map(_oracle_dirderiv_chunk, chunks)))
+    scale = max(1.0, np.max(np.abs(grad)))
+    assert abs(np.dot(grad, v) - dref) <= 1e-9 * scale * np.sum(np.abs(v)), (np.dot(grad, v), dref)

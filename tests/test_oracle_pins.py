@@ -237,13 +237,75 @@ def test_thresholds_match_eq_10_11():
         assert 0 < cp["T"] < 2 ** 31 + 1
 
 
-def test_trajectory_bound_eq6_limits():
-    """Eq. 6 grows like xi/eps^2 * log(1/delta) for small eps."""
-    t1 = O.trajectory_count_bound(1e-2, 1e-3, 0.0, 4.0)
-    t2 = O.trajectory_count_bound(1e-2, 1e-3, 0.0, 16.0)
-    assert abs(t2 / t1 - 4.0) < 1e-3
-    # with p_max = 0 it is 2 xi / eps log(2 e^2/delta)
-    assert t1 == math.ceil(2 * 4.0 / 1e-2 * math.log(2 * math.e ** 2 / 1e-3))
+def _eq6_decimal(eps, delta, pmax, xi):
+    """Eq. 6 worked out in 40-digit decimal arithmetic (an independent
+    evaluation: exact square roots and logarithm of the decimal inputs)."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 40
+    E, D, P, X = (Decimal(repr(v)) for v in (eps, delta, pmax, xi))
+    e2 = Decimal(1).exp() ** 2
+    num = (X.sqrt() + P.sqrt()) ** 2
+    den = ((P + E).sqrt() - P.sqrt()) ** 2
+    v = 2 * num / den * (2 * e2 / D).ln()
+    return int(v.to_integral_value(rounding="ROUND_CEILING")), v
+
+
+@pytest.mark.parametrize("eps,delta,pmax,xi", [(0.01, 0.05, 0.0, 4.0), (0.02, 1e-3, 0.09, 2.25),
+                                                (1e-4, 0.01, 3e-5, 6.7), (0.25, 0.5, 1.0, 1.0)])
+def test_trajectory_bound_eq6_worked_values(eps, delta, pmax, xi):
+    """Eq. 6 at four points against a 40-digit evaluation (values chosen away
+    from integer boundaries)."""
+    t_dec, v = _eq6_decimal(eps, delta, pmax, xi)
+    assert abs(float(v) - round(float(v))) > 1e-6
+    assert O.trajectory_count_bound(eps, delta, pmax, xi) == t_dec
+
+
+def test_trajectory_bound_eq6_limits_and_monotonicity():
+    """p_max = 0: 2 xi / eps log(2 e^2 / delta) (the denominator is eps);
+    eps << p_max: ~ 8 p_max (sqrt xi + sqrt p_max)^2 / eps^2 log(2 e^2 / delta)
+    ((sqrt(p + eps) - sqrt p)^2 -> eps^2 / (4 p)); monotone in every argument."""
+    L = math.log(2 * math.e ** 2 / 1e-3)
+    assert O.trajectory_count_bound(1e-2, 1e-3, 0.0, 4.0) == math.ceil(2 * 4.0 / 1e-2 * L)
+    p, xi, eps = 0.3, 5.0, 1e-5
+    approx = 8 * p * (math.sqrt(xi) + math.sqrt(p)) ** 2 / eps ** 2 * L
+    assert abs(O.trajectory_count_bound(eps, 1e-3, p, xi) / approx - 1) < 1e-4
+    base = (1e-3, 1e-2, 0.01, 3.0)
+    t0 = O.trajectory_count_bound(*base)
+    assert O.trajectory_count_bound(2e-3, 1e-2, 0.01, 3.0) < t0       # larger eps
+    assert O.trajectory_count_bound(1e-3, 2e-2, 0.01, 3.0) < t0       # larger delta
+    assert O.trajectory_count_bound(1e-3, 1e-2, 0.02, 3.0) > t0       # larger p_max
+    assert O.trajectory_count_bound(1e-3, 1e-2, 0.01, 6.0) > t0       # larger extent
+
+
+def test_splitmix64_known_answers():
+    """The Estimate rounds' seeds come from SplitMix64; pinned to its published
+    output sequence for state 0."""
+    kat = json.load(open(os.path.join(GOLD, "splitmix64_kat.json")))
+    g = 0x9E3779B97F4A7C15
+    out = [O.splitmix64((k * g) & ((1 << 64) - 1)) for k in range(1, 5)]
+    assert out == [int(h, 16) for h in kat["outputs_hex"]]
+
+
+def test_trajectory_grid():
+    """Counts round up to m * 2^e, 4 <= m <= 8: never down, at most 25 % up."""
+    for t in list(range(1, 300)) + [1023, 1024, 1025, 10 ** 6 + 7, 2 ** 31 + 1]:
+        g = O.trajectory_grid(t)
+        assert g >= t and (t <= 8 or g <= 1.25 * t)
+        e = max(0, g.bit_length() - 4)
+        assert g % (1 << e) == 0 and (g >> e) <= 15
+
+
+def test_estimate_oracle_meets_eps():
+    """The oracle's Estimate on three bitstrings of the 8-mode brick circuit:
+    within eps of the exact probability (failure probability 1e-3 each), with
+    fewer trajectories than one Raw Estimate at p_max = 1 would take."""
+    c, bits = W.brick8_exact()
+    sub = bits[[3, 17, 40]]
+    p = O.exact_probabilities(c, sub)
+    eps, delta = 0.02, 1e-3
+    ph, _, traj = O.estimate(c, sub, eps, delta, seed=11)
+    assert np.all(np.abs(ph - p) <= eps)
+    assert np.all(traj < O.trajectory_count_bound(eps, delta, 1.0, O.extent(c.gates)))
 
 
 # --------------------------------------------------------------------------- Raw Estimate
