@@ -1,18 +1,33 @@
 #!/usr/bin/env python
-"""Throughput benchmark of the Exact probability path on the LUCJ-shaped
-workload: 32 qubits (2x16 spin-orbital modes), 8 alpha + 8 beta electrons,
-one Jastrow layer of k=16 controlled-phase gates (4 aa + 4 bb nearest
-neighbour, 8 ab on-site, angles N(0, 0.1)) between a Haar orbital rotation
-and its inverse; 2^16 branches; 10^4 bitstrings uniform in the (8,8) sector.
+"""Throughput benchmark of the ExtraFerm probability path on one GB300.
 
-One step = one ef_prob_exact_dev call on device-resident bitstrings: branch
-matrices, FP32 minor LUs, FP64 branch sums, per-result error estimate and
-the FP64 recomputation of flagged results (EF_PREC_AUTO, tol 1e-5).
+Headline (the JSON line's value): the Exact algorithm on the LUCJ-shaped
+32-qubit workload (2x16 spin-orbital modes, 8 alpha + 8 beta electrons, one
+Jastrow layer of k=16 controlled-phase gates (4 aa + 4 bb nearest neighbour,
+8 ab on-site, angles N(0, 0.1)) between a Haar orbital rotation and its
+inverse; 2^16 branches; 10^4 bitstrings uniform in the (8,8) sector). One step
+= one ef_prob_exact_dev call on device-resident bitstrings: branch matrices,
+FP32 minor LUs, float-pair branch sums, per-result error estimate and the FP64
+recomputation of flagged results (EF_PREC_AUTO, tol 1e-5).
+
+The same line carries one sub-object per other workload, each with its device
+time, its dominant kernel against a measured peak and a check against the FP64
+CPU oracle (run in the CPU-baseline worker pool):
+
+  config1_brick8_exact   8 modes, eta 4, k 3, all 70 bitstrings, FP64: us per call
+  config3_lucj52_approx  52 qubits, k 152, t = ceil(extent 1e4), all 10^5 bitstrings
+  config4_batch64        64 uneven circuits in one captured graph, against the
+                         FP64 single-circuit form of the same circuits
+  config5_lucj40_grad    gradient of sum_b w_b log p_b, 4096 bitstrings, 2412 angles
+  fig4_latency           single-outcome Exact latency, random circuits of 8-36 qubits, k 16
+  peaks                  measured FP32 / FP64 FMA and Philox4x32-10 rates of this GPU
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-secondary] [--workload exact|approx|grad|batch]
 
-Under torchrun every rank runs its own replica on its own 10^4 bitstrings
-(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+Under torchrun every rank runs its own replica of the headline on its own 10^4
+bitstrings (weak scaling, no collective on the data path); rank 0 prints one
+JSON line.
 """
 from __future__ import annotations
 
@@ -40,13 +55,12 @@ UNIT = "probabilities/s"
 NB = 10_000
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_exact_lu_f32<8> launch on this workload
 # (ncu, GB300, `-k regex:"k_exact_lu_f32|k_exact_combine_wp" -s 9 -c 6` on `bench.py --steps 3
-# --warmup 3 --no-cpu-baseline --no-fp64-form`): one launch covers both mode blocks; of the 82 MB of FP32 determinants it
-# writes, 24-27 MB reach DRAM within the launch and the rest stays in L2 until the combine; the
-# pattern matrices are read from L2. To be re-measured whenever that kernel changes.
+# --warmup 3 --no-cpu-baseline --no-fp64-form --no-secondary`): one launch covers both mode blocks;
+# of the 82 MB of FP32 determinants it writes, 24-27 MB reach DRAM within the launch and the rest
+# stays in L2 until the combine; the pattern matrices are read from L2. To be re-measured whenever
+# that kernel changes.
 LU_DRAM_BYTES_PER_LAUNCH = 26_846_848  # mean of two launches (28.4 MB, 25.3 MB), 8-pattern chunks
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 L2_BYTES = 129 * 2 ** 20
-BATCH_TRAJ = 1000  # trajectories per Raw Estimate circuit of the batch workload
 WORKLOAD = ("LUCJ exact: 2x16 modes (32 qubits), 8a+8b, k=16 controlled-phase gates "
             "(4 aa + 4 bb neighbour, 8 ab on-site, N(0,0.1)), 2^16 branches, 10^4 sector bitstrings")
 
@@ -57,18 +71,43 @@ _ORACLE_CACHE = {}
 
 
 def _oracle_worker(task):
-    """Run the FP64 CPU oracle on bitstrings ``idx`` of the workload's batch
-    ``seed_rank``; returns (seconds, probabilities)."""
+    """Run the FP64 CPU oracle on bitstrings ``idx`` of the headline workload's
+    batch ``rank``; returns (seconds, probabilities)."""
     idx, rank = task
     import oracle as O
     key = ("c2", rank)
     if key not in _ORACLE_CACHE:
-        c, bits = make_workload(rank)
-        _ORACLE_CACHE[key] = (c, bits)
+        _ORACLE_CACHE[key] = make_workload(rank)
     c, bits = _ORACLE_CACHE[key]
     t0 = time.perf_counter()
     p = O.exact_probabilities(c, bits[np.asarray(idx, dtype=np.int64)])
     return time.perf_counter() - t0, p.tolist()
+
+
+def _oracle_task(task):
+    """Oracle legs of the secondary workloads: (name, args) -> (seconds, result)."""
+    import oracle as O
+    name, args = task
+    t0 = time.perf_counter()
+    if name == "brick8":
+        c, bits = W.brick8_exact()
+        res = O.exact_probabilities(c, bits).tolist()
+    elif name == "lucj52":
+        i, t = args
+        c, bits = W.lucj52_approx(100_000)
+        res = O.raw_estimate(c, bits[[i]], t=t, seed=1, b_indices=[i])[0].tolist()
+    elif name == "lucj40":
+        idx, v = args
+        c, bits, w = W.lucj40_grad()
+        p = O.exact_probabilities(c, bits[idx])
+        res = [O.prob_directional_derivative(c, bits[idx], w[idx] / p, np.asarray(v)), p.tolist()]
+    elif name == "batch":
+        i, nbits = args
+        c, bits, _ = W.uneven_batch64()[i]
+        res = O.exact_probabilities(c, bits[:nbits]).tolist()
+    else:
+        raise ValueError(name)
+    return time.perf_counter() - t0, res
 
 
 def make_workload(rank: int = 0):
@@ -152,7 +191,7 @@ def stop_clock_sampler(handle, path, t_begin, t_end):
             "reasons": reasons, "samples": len(sel)}
 
 
-# ----------------------------------------------------------------------------- arms
+# ----------------------------------------------------------------------------- helpers
 
 
 def dist_setup(args):
@@ -183,6 +222,49 @@ def aggregate_timing(local_ms: float, world: int, nb: int, steps: int, dist=None
     return worst, world * nb * steps / (worst / 1e3)
 
 
+def lu_flops(eta: int) -> float:
+    """Algorithmic flops of one eta x eta complex LU with partial pivoting
+    (complex multiply-add 8, multiply 6, reciprocal and pivot ~17 per step)."""
+    return 17.0 * eta + sum(8.0 * (eta - k - 1) ** 2 + 6.0 * (eta - k - 1) for k in range(eta))
+
+
+def timed_device(torch, dev, stream, flush, fn, steps, warmup):
+    """Device ms of each of `steps` calls after `warmup` untimed ones, L2 flushed
+    before every call outside its events."""
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize(dev)
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def measured_peaks(ef, torch):
+    """FP32 (scalar and packed FMA), FP64 FMA and Philox4x32-10 rates of this GPU."""
+    p = {"sm_count": torch.cuda.get_device_properties(0).multi_processor_count}
+    f32 = ef.ef_measure_peak(ef.PEAK_FP32)
+    f32x2 = ef.ef_measure_peak(ef.PEAK_FP32X2)
+    p["fp32_scalar_tflops"] = f32 / 1e12
+    p["fp32_packed_tflops"] = f32x2 / 1e12
+    p["fp32_tflops"] = max(f32, f32x2) / 1e12
+    p["fp64_tflops"] = ef.ef_measure_peak(ef.PEAK_FP64) / 1e12
+    p["philox_blocks_per_s"] = ef.ef_measure_peak(ef.PEAK_PHILOX)
+    p["how"] = ("ef_measure_peak: independent FMA chains (or Philox4x32-10 counters) in every lane of "
+                "8 CTAs x 256 threads per SM, best of 5 launches after a warm-up, CUDA events")
+    return p
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -211,27 +293,292 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- secondary workloads
+
+
+def bench_config1(ef, torch, dev, stream, flush, pool, ncores):
+    """8 modes, eta 4, brick layer, k 3 controlled phases, all 70 sector bitstrings, FP64."""
+    c, bits = W.brick8_exact()
+    h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
+    d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
+    d_out = torch.empty(len(bits), dtype=torch.float64, device=dev)
+    fut = pool.apply_async(_oracle_task, (("brick8", None),)) if pool else None
+
+    def fn():
+        ef.ef_prob_exact_dev(h, d_bits.data_ptr(), len(bits), d_out.data_ptr(), 0, stream.cuda_stream)
+    ms = timed_device(torch, dev, stream, flush, fn, 20, 5)
+    st = ef.ef_circuit_get_stats(h)
+    p = d_out.cpu().numpy()
+    t0 = time.perf_counter()
+    for _ in range(20):
+        ef.ef_prob_exact(h, bits)
+    host_us = (time.perf_counter() - t0) / 20 * 1e6
+    ef.ef_circuit_destroy(h)
+    out = {"workload": "brick layer, 8 modes, eta 4 (modes 0-3), k=3 controlled phases U[0, pi/4], "
+                       "all C(8,4)=70 bitstrings, EF_PREC_FP64",
+           "us_per_call": 1e3 * statistics.median(ms), "host_us_per_call": host_us, "steps": 20, "warmup": 5,
+           "probabilities_per_s": len(bits) / (statistics.median(ms) / 1e3),
+           "kernel_launches_per_call": st["kernel_launches"],
+           "roofline": {"bound": "latency", "note": "560 branch-dets of 4x4: launch latency, not a pipe, "
+                                                      "bounds the call"}}
+    if fut is not None:
+        wall, p_ref = fut.get()
+        p_ref = np.array(p_ref)
+        floor = 1e-6 / 70
+        out["max_rel_err_vs_oracle"] = float(np.max(np.abs(p - p_ref) / np.maximum(p_ref, floor)))
+        out["cpu_baseline"] = {"value": len(bits) / wall, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "all 70 bitstrings, one core"}
+    return out
+
+
+def bench_config3(ef, torch, dev, stream, flush, pool, peaks):
+    """52-qubit LUCJ Raw Estimate at t = ceil(extent 1e4) on all 10^5 bitstrings, EF_PREC_AUTO."""
+    c, bits = W.lucj52_approx(100_000)
+    h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_AUTO, tol=1e-5,
+                             flags=ef.EF_FLAG_TIME_KERNELS)
+    t = W.lucj52_trajectories(ef.ef_circuit_extent(h))
+    nb = len(bits)
+    idx = [5, 77_777]
+    futs = [pool.apply_async(_oracle_task, (("lucj52", (i, t)),)) for i in idx] if pool else []
+    d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
+    d_out = torch.empty(nb, dtype=torch.float64, device=dev)
+    d_se = torch.empty(nb, dtype=torch.float64, device=dev)
+    d_err = torch.empty(nb, dtype=torch.float64, device=dev)
+    kern = []
+
+    def fn():
+        ef.ef_prob_approx_dev(h, d_bits.data_ptr(), nb, t, 1, 0, d_out.data_ptr(), d_se.data_ptr(),
+                              stream.cuda_stream, d_err=d_err.data_ptr())
+    ms = timed_device(torch, dev, stream, flush, fn, 2, 3)
+    st = ef.ef_circuit_get_stats(h)
+    kern_ms = st["dominant_kernel_ms"]
+    p = d_out.cpu().numpy()
+    err = d_err.cpu().numpy()
+    ef.ef_circuit_destroy(h)
+    per = statistics.mean(ms)
+    traj_s = nb * t / (per / 1e3)
+    k = c.n_cphase
+    blocks = nb * t * ((k + 3) // 4)
+    achieved = blocks / (kern_ms / 1e3)
+    out = {"workload": f"LUCJ 52 qubits: 2x26 modes, 5a+5b, 2 layers, k=152 U[-0.05,0.05], t = ceil(extent 1e4) "
+                       f"= {t} trajectories per bitstring, all {nb} sector bitstrings, EF_PREC_AUTO (FP32 "
+                       f"minors, FP64 recompute of results whose estimated error exceeds 1e-5)",
+           "value": nb / (per / 1e3), "unit": UNIT, "ms_per_step": per, "steps": len(ms), "warmup": 3,
+           "trajectories_per_s": traj_s, "fp64_recomputed": st["fp64_recomputed"],
+           "sampled_flips": st["sampled_flips"], "max_est_rel_err": float(np.max(np.abs(err))),
+           "dominant_kernel_ms": kern_ms,
+           "roofline": {"bound": "alu", "kernel": "k_approx (Philox4x32-10 sampling, one word per gate)",
+                        "achieved": achieved, "peak": peaks["philox_blocks_per_s"], "unit": "Philox blocks/s",
+                        "frac": achieved / peaks["philox_blocks_per_s"],
+                        "peak_source": "measured (ef_measure_peak kind 3) on this GPU",
+                        "work": f"ceil(k/4) = {(k + 3) // 4} Philox4x32-10 blocks per trajectory"}}
+    if futs:
+        got = [f.get() for f in futs]
+        wall = sum(g[0] for g in got)
+        p_ref = np.array([g[1][0] for g in got])
+        floor = 1e-6 / math.comb(26, 5) ** 2
+        out["oracle_check"] = {"bitstrings": idx, "max_rel_err": float(np.max(np.abs(p[idx] - p_ref) /
+                                                                               np.maximum(p_ref, floor)))}
+        out["cpu_baseline"] = {"value": len(idx) / wall, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{len(idx)} bitstrings at the full t (same trajectories), one core "
+                                         f"each"}
+    return out
+
+
+def bench_config5(ef, torch, dev, stream, flush, pool, peaks):
+    """Gradient of sum_b w_b log p_b over 4096 bitstrings of the 40-qubit LUCJ circuit, FP64 adjoint."""
+    c, bits, w = W.lucj40_grad()
+    nb = len(bits)
+    h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64,
+                             flags=ef.EF_FLAG_TIME_KERNELS)
+    na = ef.ef_circuit_num_angles(h)
+    v = np.random.default_rng(21).normal(size=na)
+    sub = list(range(16))
+    fut = pool.apply_async(_oracle_task, (("lucj40", (sub, v.tolist())),)) if pool else None
+    d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
+    d_gp = torch.empty(nb, dtype=torch.float64, device=dev)
+    d_p = torch.empty(nb, dtype=torch.float64, device=dev)
+    d_g = torch.empty(na, dtype=torch.float64, device=dev)
+    ef.ef_prob_exact_dev(h, d_bits.data_ptr(), nb, d_p.data_ptr(), 0, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    d_gp.copy_(torch.from_numpy(w).to(dev) / d_p.clamp_min(1e-300))
+
+    def fn():
+        ef.ef_prob_grad_dev(h, d_bits.data_ptr(), nb, d_gp.data_ptr(), d_p.data_ptr(), d_g.data_ptr(),
+                            stream.cuda_stream)
+    ms = timed_device(torch, dev, stream, flush, fn, 5, 3)
+    st = ef.ef_circuit_get_stats(h)
+    g = d_g.cpu().numpy()
+    ef.ef_circuit_destroy(h)
+    per = statistics.mean(ms)
+    # FP64 work of the adjoint kernels: per (block, pattern, bitstring) an in-place
+    # eta x eta inverse (eta^3 complex multiply-adds) and the eta^2 cotangent products
+    eta, r = 6, 8
+    flops = 2 * (2 ** r) * nb * (8.0 * eta ** 3 + 6.0 * eta ** 2)
+    kern_ms = st["dominant_kernel_ms"]
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    out = {"workload": f"LUCJ 40 qubits: 2x20 modes, 6a+6b, 2 layers, k=12, {nb} bitstrings, gradient of "
+                       f"sum w_b log p_b w.r.t. {na} angles, EF_PREC_FP64 adjoint",
+           "ms_per_gradient": per, "steps": len(ms), "warmup": 3, "value": nb / (per / 1e3),
+           "unit": "bitstring gradients/s", "dominant_kernel_ms": kern_ms,
+           "roofline": {"bound": "fp64", "kernel": "k_grad_combine + k_grad_minors (per-minor inverse, "
+                                                     "cotangents, layer sweep)",
+                        "achieved": achieved, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                        "frac": achieved / peaks["fp64_tflops"],
+                        "peak_source": "measured (ef_measure_peak kind 2) on this GPU",
+                        "work": "2 blocks x 2^8 patterns x 4096 bitstrings x (8 eta^3 + 6 eta^2), eta 6"}}
+    if fut is not None:
+        wall, (dref, p_ref) = fut.get()
+        # the oracle's directional derivative over the first 16 bitstrings, against
+        # a GPU gradient over the same 16 (a separate small call)
+        h2 = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
+        _, g16 = ef.ef_prob_grad(h2, bits[sub], w[sub] / np.array(p_ref))
+        ef.ef_circuit_destroy(h2)
+        scale = max(1.0, float(np.max(np.abs(g16)))) * float(np.sum(np.abs(v)))
+        out["oracle_check"] = {"bitstrings": 16, "directions": 1,
+                               "rel_err": abs(float(np.dot(g16, v)) - dref) / scale}
+        out["cpu_baseline"] = {"value": len(sub) / wall, "unit": "bitstring directional derivatives/s",
+                               "cores": 1, "kind": "oracle",
+                               "sample": "forward-mode derivative along one direction, 16 bitstrings, one core "
+                                         f"(a full gradient takes {na} directions)"}
+    out["grad_norm"] = float(np.linalg.norm(g))
+    return out
+
+
+def bench_config4(ef, torch, dev, stream, flush, pool, peaks):
+    """64 uneven circuits in one captured graph (Exact for k <= 14, Raw Estimate with
+    t = min(ceil(extent 1e4), 1e6) otherwise), against the FP64 single-circuit form."""
+    batch = W.uneven_batch64()
+    hs, dbits, outs, nb, traj = [], [], [], [], []
+    for cc, bits, mode in batch:
+        h = ef.ef_circuit_create(cc.n_modes, cc.occupation, cc.gates, precision=ef.EF_PREC_AUTO)
+        hs.append(h)
+        dbits.append(torch.from_numpy(bits.view(np.int64)).to(dev))
+        outs.append(torch.empty(len(bits), dtype=torch.float64, device=dev))
+        nb.append(len(bits))
+        xi = ef.ef_circuit_extent(h)
+        traj.append(0 if mode == "exact" else int(min(math.ceil(xi * 1e4), 10 ** 6)))
+    ex = [i for i, t in enumerate(traj) if t == 0 and batch[i][0].n_modes <= 24][:2]
+    futs = [pool.apply_async(_oracle_task, (("batch", (i, 4)),)) for i in ex] if pool else []
+    b = ef.ef_batch_create(hs)
+    ptr_b, ptr_o = [d.data_ptr() for d in dbits], [o.data_ptr() for o in outs]
+
+    def fn():
+        ef.ef_batch_prob_dev(b, ptr_b, nb, ptr_o, traj, 7, stream.cuda_stream)
+    ms = timed_device(torch, dev, stream, flush, fn, 1, 1)  # the warm-up call plans, runs and captures
+    launches = ef.ef_batch_get_stats(b)["kernel_launches"]
+    p_batch = [o.cpu().numpy() for o in outs]
+    ef.ef_batch_destroy(b)
+    per = statistics.mean(ms)
+    total_nb = sum(nb)
+    # the plain FP64 single-circuit form over the same circuits: one call per circuit on
+    # the first max(256, nb/8) of its bitstrings (all of them below 256), after a warm-up
+    # call that sizes its buffers, scaled to the circuit's bitstring count
+    ms64 = 0.0
+    max_rel = 0.0
+    sampled = 0
+    for i, (cc, bits, mode) in enumerate(batch):
+        h64 = ef.ef_circuit_create(cc.n_modes, cc.occupation, cc.gates, precision=ef.EF_PREC_FP64)
+        ns = min(nb[i], max(256, -(-nb[i] // 8)))
+        sampled += ns
+        o64 = torch.empty(ns, dtype=torch.float64, device=dev)
+
+        def call(t):
+            if t == 0:
+                ef.ef_prob_exact_dev(h64, ptr_b[i], ns, o64.data_ptr(), 0, stream.cuda_stream)
+            else:
+                ef.ef_prob_approx_dev(h64, ptr_b[i], ns, t, 7, 0, o64.data_ptr(), 0, stream.cuda_stream)
+        warm_t = 0 if traj[i] == 0 else min(traj[i], 256 * max(1, -(-peaks["sm_count"] * 12 // ns)))
+        call(warm_t)
+        torch.cuda.synchronize(dev)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call(traj[i])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 += e0.elapsed_time(e1) * nb[i] / ns
+        p64 = o64.cpu().numpy()
+        floor = 1e-6 / math.comb(cc.n_modes // 2, len(cc.occupied_modes()) // 2) ** 2
+        max_rel = max(max_rel, float(np.max(np.abs(p_batch[i][:ns] - p64) / np.maximum(p64, floor))))
+        ef.ef_circuit_destroy(h64)
+    for h in hs:
+        ef.ef_circuit_destroy(h)
+    n_exact = sum(1 for t in traj if t == 0)
+    out = {"workload": f"64 circuits, n in 12..40, {total_nb} bitstrings, {n_exact} Exact (EF_PREC_AUTO), "
+                       f"{64 - n_exact} Raw Estimate with t = min(ceil(extent 1e4), 1e6) "
+                       f"({sum(nb[i] * traj[i] for i in range(64)):.3e} trajectories); one captured graph",
+           "value": total_nb / (per / 1e3), "unit": UNIT, "ms_per_step": per, "steps": 1,
+           "warmup": 1, "warmup_note": "the first call plans, runs and captures the graph; the timed call replays it",
+           "kernel_launches_per_step": launches,
+           "fp64_single_circuit": {"value": total_nb / (ms64 / 1e3), "unit": UNIT, "ms": ms64,
+                                   "form": "EF_PREC_FP64, one call per circuit (same bitstrings, same seed), "
+                                           f"timed on the first max(256, nb/8) bitstrings of each circuit "
+                                           f"({sampled} in all) and scaled to its bitstring count"},
+           "batched_over_fp64_single": ms64 / per,
+           "max_rel_diff_vs_fp64_form": max_rel,
+           "roofline": {"bound": "alu", "kernel": "k_approx of the Raw Estimate circuits (the bulk of the work)",
+                        "note": "whole-graph time; the Raw Estimate share is measured in config3_lucj52_approx"}}
+    if futs:
+        errs, walls = [], 0.0
+        for i, f in zip(ex, futs):
+            wall, p_ref = f.get()
+            walls += wall
+            cc = batch[i][0]
+            floor = 1e-6 / math.comb(cc.n_modes // 2, len(cc.occupied_modes()) // 2) ** 2
+            errs.append(float(np.max(np.abs(p_batch[i][:4] - np.array(p_ref)) / np.maximum(p_ref, floor))))
+        out["oracle_check"] = {"circuits": ex, "bitstrings_each": 4, "max_rel_err": max(errs)}
+        out["cpu_baseline"] = {"value": 4 * len(ex) / walls, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"4 bitstrings of each of {len(ex)} Exact circuits, one core"}
+    return out
+
+
+def bench_fig4(ef, torch, dev, stream, flush):
+    """Single-outcome Exact latency on random extended matchgate circuits (Fig. 4's
+    workload: k = 16 controlled phases on random mode pairs, matchgates in proportion
+    to the size), 8 to 36 qubits at half filling."""
+    rows = []
+    for n in range(8, 37, 4):
+        c = W.random_fig4_circuit(n, n // 2, 16, 4, seed=100 + n, angle_std=1.0)
+        bits = W.sector_bitstrings(n, n // 2, 1, np.random.default_rng(n))
+        d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
+        d_out = torch.empty(1, dtype=torch.float64, device=dev)
+        row = {"qubits": n, "eta": n // 2, "k": 16, "givens": int(np.count_nonzero(c.gates["kind"] == W.GIVENS))}
+        for name, prec in (("fp64", ef.EF_PREC_FP64), ("auto", ef.EF_PREC_AUTO)):
+            h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=prec)
+
+            def fn():
+                ef.ef_prob_exact_dev(h, d_bits.data_ptr(), 1, d_out.data_ptr(), 0, stream.cuda_stream)
+            ms = timed_device(torch, dev, stream, flush, fn, 5, 3)
+            t0 = time.perf_counter()
+            for _ in range(5):
+                ef.ef_prob_exact(h, bits)
+            row[f"{name}_device_ms"] = statistics.median(ms)
+            row[f"{name}_host_ms"] = (time.perf_counter() - t0) / 5 * 1e3
+            ef.ef_circuit_destroy(h)
+        rows.append(row)
+    return {"workload": "random extended matchgate circuits (Fig. 4): n = 8..36 qubits, eta = n/2, k = 16 "
+                        "controlled phases N(0, 1) on random mode pairs, 4 brick layers of Givens rotations, one "
+                        "sector bitstring, Exact", "rows": rows}
+
+
+# ----------------------------------------------------------------------------- headline arm
+
+
 def time_fp64_form(ef, torch, c, d_bits, p_gpu, flush, stream, dev, steps):
     """Device time of the EF_PREC_FP64 single-circuit form on the same bitstrings
     and the largest relative difference of the headline results from it."""
     h64 = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
     d_out64 = torch.empty(NB, dtype=torch.float64, device=dev)
-    steps64 = min(steps, 5)
-    ms64 = []
-    for i in range(1 + steps64):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+
+    def fn():
         ef.ef_prob_exact_dev(h64, d_bits.data_ptr(), NB, d_out64.data_ptr(), 0, stream.cuda_stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if i >= 1:
-            ms64.append(e0.elapsed_time(e1))
+    ms64 = timed_device(torch, dev, stream, flush, fn, min(steps, 5), 3)
     ef.ef_circuit_destroy(h64)
     p64 = d_out64.cpu().numpy()
     floor64 = 1e-6 / math.comb(16, 8) ** 2
     return {"value": NB / (statistics.mean(ms64) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(ms64),
-            "steps": steps64, "form": "EF_PREC_FP64 single circuit, same bitstrings, L2 flushed",
+            "steps": len(ms64), "warmup": 3, "form": "EF_PREC_FP64 single circuit, same bitstrings, L2 flushed",
             "max_rel_diff_of_value_results": float(np.max(np.abs(p_gpu - p64) / np.maximum(p64, floor64)))}
 
 
@@ -252,6 +599,7 @@ def run_ours(args):
     ef.load()
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
+    peaks = measured_peaks(ef, torch)
     c, bits = make_workload(rank)
     prec = {"auto": ef.EF_PREC_AUTO, "fp64": ef.EF_PREC_FP64, "fp32": ef.EF_PREC_FP32_MINOR}[args.precision]
     h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=prec, tol=1e-5,
@@ -325,7 +673,6 @@ def run_ours(args):
     if pool is not None:
         per_core = max(1, int(math.ceil(64 / ncores)))
         wall, idx, p_ref = time_oracle(pool, ncores, per_core)
-        pool.close()
         floor = 1e-6 / math.comb(16, 8) ** 2
         max_rel = float(np.max(np.abs(p_gpu[idx] - p_ref) / np.maximum(p_ref, floor)))
         cpu = {"value": len(idx) / wall, "unit": UNIT, "cores": ncores, "kind": "oracle",
@@ -339,6 +686,7 @@ def run_ours(args):
 
     kern_s = kern_ms / 1e3
     achieved = kern_flops / kern_s / 1e12 if kern_s > 0 else 0.0
+    ef.ef_circuit_destroy(h)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -351,18 +699,27 @@ def run_ours(args):
         "branch_dets_per_s": branch_dets,
         "executed_lus_per_step": last["executed_minor_lus"],
         "fp64_recomputed_per_step": recomputed / args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": LU_DRAM_BYTES_PER_LAUNCH,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peaks["fp32_tflops"], "traffic": LU_DRAM_BYTES_PER_LAUNCH,
                      "kernel": "k_exact_lu_f32 (FP32 LU of the per-block minors)",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+                     "peak_source": "measured FP32 FMA rate of this GPU (ef_measure_peak, the larger of scalar "
+                                    "and packed FFMA2), of measured"},
         "dominant_kernel_ms_per_step": kern_ms / args.steps,
         "fp64_single_circuit": fp64_form,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": NB * 16, "d2h_bytes_per_step": NB * 8},
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "peaks": peaks,
     }
-    ef.ef_circuit_destroy(h)
+    if rank == 0 and world == 1 and not args.no_secondary:
+        line["config1_brick8_exact"] = bench_config1(ef, torch, dev, stream, flush, pool, ncores)
+        line["config5_lucj40_grad"] = bench_config5(ef, torch, dev, stream, flush, pool, peaks)
+        line["fig4_latency"] = bench_fig4(ef, torch, dev, stream, flush)
+        line["config3_lucj52_approx"] = bench_config3(ef, torch, dev, stream, flush, pool, peaks)
+        line["config4_batch64"] = bench_config4(ef, torch, dev, stream, flush, pool, peaks)
+    if pool is not None:
+        pool.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -370,29 +727,8 @@ def run_ours(args):
     return 0
 
 
-
-# ----------------------------------------------------------------------------- secondary workloads
-# (`--workload approx|grad|batch`): one JSON line each, device time with CUDA events, L2 flushed
-# between steps; the default run measures the Exact workload above.
-
-
-def _timed_steps(torch, dev, stream, flush, fn, steps, warmup):
-    for _ in range(warmup):
-        fn()
-    torch.cuda.synchronize(dev)
-    ms = []
-    for _ in range(steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms.append(e0.elapsed_time(e1))
-    return ms
-
-
 def run_secondary(args):
+    """One secondary workload alone (profiling runs): --workload approx|grad|batch."""
     import torch
     import paper_2511_12416_gb300 as ef
 
@@ -401,9 +737,7 @@ def run_secondary(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "data": "synthetic", "workload_kind": args.workload}
-    launches = 0
+    peaks = measured_peaks(ef, torch)
     if args.workload == "approx":
         c, bits = W.lucj52_approx(args.nb)
         h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP32_MINOR)
@@ -417,72 +751,17 @@ def run_secondary(args):
             seed[0] += 1
             ef.ef_prob_approx_dev(h, d_bits.data_ptr(), len(bits), t, seed[0], 0, d_out.data_ptr(),
                                   d_se.data_ptr(), stream.cuda_stream)
-        ms = _timed_steps(torch, dev, stream, flush, fn, args.steps, args.warmup)
-        launches = ef.ef_circuit_get_stats(h)["kernel_launches"]
+        ms = timed_device(torch, dev, stream, flush, fn, args.steps, args.warmup)
         ef.ef_circuit_destroy(h)
         per = statistics.mean(ms)
-        line.update({"metric": "Raw Estimate probabilities/s (FP32 minors, FP64 trajectory sums)",
-                     "value": len(bits) / (per / 1e3), "unit": "probabilities/s", "ms_per_step": per,
-                     "dtype": "f32",
-                     "trajectories_per_s": len(bits) * t / (per / 1e3),
-                     "config": {"workload": f"LUCJ 52-qubit approximate: 2x26 modes, 5a+5b, 2 layers, k=152, "
-                                            f"t = ceil(extent/1e-4) = {t} trajectories per bitstring, "
-                                            f"{len(bits)} of the 10^5 sector bitstrings per step",
-                                "l2": "flushed between timed steps"}})
+        line = {"workload_kind": "approx", "metric": "Raw Estimate probabilities/s (FP32 minors)",
+                "value": len(bits) / (per / 1e3), "unit": UNIT, "ms_per_step": per,
+                "trajectories_per_s": len(bits) * t / (per / 1e3), "t": t, "nb": len(bits)}
     elif args.workload == "grad":
-        c, bits, w = W.lucj40_grad()
-        h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_FP64)
-        d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
-        d_gp = torch.empty(len(bits), dtype=torch.float64, device=dev)
-        d_p = torch.empty(len(bits), dtype=torch.float64, device=dev)
-        d_g = torch.empty(ef.ef_circuit_num_angles(h), dtype=torch.float64, device=dev)
-        ef.ef_prob_exact_dev(h, d_bits.data_ptr(), len(bits), d_p.data_ptr(), 0, stream.cuda_stream)
-        torch.cuda.synchronize(dev)
-        # d/dp of sum_b w_b log p_b
-        d_gp.copy_(torch.from_numpy(w).to(dev) / d_p.clamp_min(1e-300))
-
-        def fn():
-            ef.ef_prob_grad_dev(h, d_bits.data_ptr(), len(bits), d_gp.data_ptr(), d_p.data_ptr(), d_g.data_ptr(),
-                                stream.cuda_stream)
-        ms = _timed_steps(torch, dev, stream, flush, fn, args.steps, args.warmup)
-        launches = ef.ef_circuit_get_stats(h)["kernel_launches"]
-        n_ang = ef.ef_circuit_num_angles(h)
-        ef.ef_circuit_destroy(h)
-        per = statistics.mean(ms)
-        line.update({"metric": "bitstring gradients/s (d p_b / d every angle, FP64 adjoint)",
-                     "value": len(bits) / (per / 1e3), "unit": "bitstrings/s", "ms_per_step": per, "dtype": "f64",
-                     "config": {"workload": f"LUCJ 40-qubit: 2x20 modes, 6a+6b, 2 layers, k=12, {len(bits)} "
-                                            f"bitstrings, gradient of sum w_b log p_b w.r.t. {n_ang} angles",
-                                "l2": "flushed between timed steps"}})
-    else:  # batch
-        batch = W.uneven_batch64()
-        hs, dbits, outs, nb, traj = [], [], [], [], []
-        for cc, bits, mode in batch:
-            hs.append(ef.ef_circuit_create(cc.n_modes, cc.occupation, cc.gates, precision=ef.EF_PREC_AUTO))
-            dbits.append(torch.from_numpy(bits.view(np.int64)).to(dev))
-            outs.append(torch.empty(len(bits), dtype=torch.float64, device=dev))
-            nb.append(len(bits))
-            traj.append(0 if mode == "exact" else BATCH_TRAJ)
-        b = ef.ef_batch_create(hs)
-        ptr_b, ptr_o = [d.data_ptr() for d in dbits], [o.data_ptr() for o in outs]
-
-        def fn():
-            ef.ef_batch_prob_dev(b, ptr_b, nb, ptr_o, traj, 7, stream.cuda_stream)
-        ms = _timed_steps(torch, dev, stream, flush, fn, args.steps, args.warmup)
-        launches = ef.ef_batch_get_stats(b)["kernel_launches"]
-        ef.ef_batch_destroy(b)
-        for h in hs:
-            ef.ef_circuit_destroy(h)
-        per = statistics.mean(ms)
-        n_exact = sum(1 for t in traj if t == 0)
-        line.update({"metric": "probabilities/s over an uneven 64-circuit batch (one captured graph)",
-                     "value": sum(nb) / (per / 1e3), "unit": "probabilities/s", "ms_per_step": per, "dtype": "f32",
-                     "circuits_per_s": len(hs) / (per / 1e3),
-                     "config": {"workload": f"64 circuits, n in 12..40, {sum(nb)} bitstrings, {n_exact} Exact "
-                                            f"(EF_PREC_AUTO), {len(hs) - n_exact} Raw Estimate with {BATCH_TRAJ} "
-                                            f"trajectories each; graph replay per step",
-                                "l2": "flushed between timed steps"}})
-    line["gpu_launches"] = launches
+        line = {"workload_kind": "grad", **bench_config5(ef, torch, dev, stream, flush, None, peaks)}
+    else:
+        line = {"workload_kind": "batch", **bench_config4(ef, torch, dev, stream, flush, None, peaks)}
+    line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "peaks": peaks})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -497,9 +776,10 @@ def main():
     ap.add_argument("--precision", choices=["auto", "fp64", "fp32"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the FP64 single-circuit form")
+    ap.add_argument("--no-secondary", action="store_true", help="headline only (no other workloads)")
     ap.add_argument("--nb", type=int, default=10_000, help="bitstrings per GPU (profiling runs use fewer)")
     ap.add_argument("--workload", choices=["exact", "approx", "grad", "batch"], default="exact",
-                    help="exact: the headline line; the others measure the remaining paths, one line each")
+                    help="exact: the full line; the others measure one secondary path alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -181,7 +181,7 @@ int ef_prob_exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double*
  * LU of the rank-one-updated minor instead.
  * err_out[nb] (nullable): estimated relative error of p_hat, the rounding of
  * the FP32 path against the same estimator in exact arithmetic (0 on the FP64
- * path). Under EF_PREC_AUTO (blocks of at most 8 particles) bitstrings whose
+ * path). Under EF_PREC_AUTO bitstrings whose
  * estimate exceeds tol are recomputed in FP64 with the same trajectories and
  * their err_out is the triggering estimate, negated. */
 int ef_prob_approx(ef_circuit* c, const uint64_t* bits, int64_t nb, int64_t n_traj, uint64_t seed,
@@ -285,6 +285,13 @@ int ef_batch_get_stats(ef_batch* b, ef_stats* st);
 
 /* Counters and timings of the circuit's last probability call (waits for it). */
 int ef_circuit_get_stats(ef_circuit* c, ef_stats* st);
+
+/* Measured throughput of the current GPU, for roofline denominators (the
+ * paper has no counterpart): kind 0 = FP32 FMA flops/s (scalar FFMA), 1 = FP32
+ * FMA flops/s (packed FFMA2), 2 = FP64 FMA flops/s, 3 = Philox4x32-10 blocks/s.
+ * Independent dependency chains in every lane of 8 CTAs per SM; best of `reps`
+ * timed launches after one warm-up; synchronous; allocates a small buffer. */
+int ef_measure_peak(int32_t kind, int32_t reps, double* rate);
 
 #ifdef __cplusplus
 }

@@ -77,6 +77,7 @@ SIGNATURES = {
     "ef_batch_prob_dev": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P),
                                          ctypes.POINTER(_I64), _U64, _P]),
     "ef_batch_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(EfStats)]),
+    "ef_measure_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _DP]),
 }
 
 _lib = None
@@ -308,3 +309,14 @@ class Circuit:
             self.close()
         except Exception:
             pass
+
+
+PEAK_FP32, PEAK_FP32X2, PEAK_FP64, PEAK_PHILOX = 0, 1, 2, 3
+
+
+def ef_measure_peak(kind: int, reps: int = 5) -> float:
+    """Measured rate of the current GPU: flops/s (FP32 scalar, FP32 packed,
+    FP64) or Philox4x32-10 blocks/s."""
+    r = ctypes.c_double()
+    _check(load().ef_measure_peak(int(kind), int(reps), ctypes.byref(r)))
+    return r.value

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["ef_api.cu", "ef_exact.cu", "ef_lu32.cu", "ef_approx.cu", "ef_grad.cu"]
+SOURCES = ["ef_api.cu", "ef_exact.cu", "ef_lu32.cu", "ef_approx.cu", "ef_grad.cu", "ef_peak.cu"]
 LIBNAME = "libextraferm.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

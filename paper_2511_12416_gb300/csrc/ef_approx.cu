@@ -28,11 +28,17 @@
 //   H_l  = -2 (Lambda_l[:, N_l] + sum_{l' > l} H_{l'} Pi_{l'-1..l}[N_{l'}, N_l]),
 // and factors it (eta x eta LU with partial pivoting).
 //
-// FP32 error bound: K is rounded to FP32 and the small determinants are
-// formed in FP32; every flipped trajectory adds a first-order bound of its
-// rounding error (units of u = 2^-24, the closed forms' input and operation
-// roundings, or the LU's pivot proxy) to a per-result sum, which the
-// finalisation turns into an estimate of the error of p_hat. det A0 is FP64.
+// FP32 error estimate: K is rounded to FP32 and the small determinants are
+// formed in FP32; every flipped trajectory s has a first-order bound e_s of its
+// rounding error (units of u = 2^-24: the closed forms' input and operation
+// roundings, or the LU's pivot proxy). The errors of distinct trajectories
+// are independent roundings, those of repeats of one trajectory are equal, so
+// the error of alpha_hat is estimated as K u sqrt(n_max sum_s e_s^2) / t with
+// n_max an upper estimate of any flipped trajectory's multiplicity (computed
+// on the host from the most probable flipped trajectory) and K = 0.5
+// (calibrated against FP64 on the same trajectories); the finalisation turns
+// it into an estimate of the relative error of p_hat.
+// det A0 is FP64, so trajectories without flips carry no error.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -181,7 +187,7 @@ __device__ __forceinline__ cplx_t<R> kdet3(const cplx_t<R>* __restrict__ K, int 
 // A(x) = A0 + sum_l H_l rho_l[N_l, :] built from the flipped modes Nl[l - 1]
 // of the layers set in lflag, then an eta x eta LU with partial pivoting.
 template <typename R, int ETA>
-__device__ __forceinline__ cplx_t<R> rank_one_det(const ApproxBlockDev& blk, const cplx_t<R>* __restrict__ sA0,
+__device__ __noinline__ cplx_t<R> rank_one_det(const ApproxBlockDev& blk, const cplx_t<R>* __restrict__ sA0,
                                                   const cplx_t<R>* __restrict__ sLeft, uint32_t lflag,
                                                   const uint64_t* Nl_in, cplx_t<R> (&hs)[kMaxApproxStored][ETA],
                                                   int (&htag)[kMaxApproxStored], R& er2, R& zabs2) {
@@ -235,7 +241,89 @@ __device__ __forceinline__ cplx_t<R> rank_one_det(const ApproxBlockDev& blk, con
     return lu_det_regs<R, ETA>(M, er2, zabs2);
 }
 
-// A trajectory deferred from the main loop (more than three flipped pairs in
+// The same for large FP64 minors: rolled loops over a matrix in local memory
+// (a few deferred trajectories per thread; unrolled, the FP64 code for
+// 9..13 particles spills heavily and takes minutes to compile). Determinant only.
+template <typename R, int ETA>
+__device__ __noinline__ cplx_t<R> rank_one_det_loop(const ApproxBlockDev& blk, const cplx_t<R>* __restrict__ sA0,
+                                                    const cplx_t<R>* __restrict__ sLeft, uint32_t lflag,
+                                                    const uint64_t* Nl_in, cplx_t<R> (&hs)[kMaxApproxStored][ETA],
+                                                    int (&htag)[kMaxApproxStored]) {
+    using T = cplx_t<R>;
+    const int n = blk.n, Lb = blk.L, eta = blk.eta;
+    const T* P = reinterpret_cast<const T*>(blk.P);
+    const T* RC = reinterpret_cast<const T*>(blk.RC);
+    T M[ETA][ETA];
+#pragma unroll 1
+    for (int i = 0; i < eta; ++i)
+#pragma unroll 1
+        for (int j = 0; j < eta; ++j) M[i][j] = sA0[i * ETA + j];
+    int nst = 0;
+#pragma unroll 1
+    for (int l = Lb; l >= 1; --l) {
+        if (!((lflag >> (l - 1)) & 1u)) continue;
+        uint64_t Nl = Nl_in[l - 1];
+        const bool store = (lflag & ((1u << (l - 1)) - 1u)) != 0;
+        const int nabove = nst;
+        while (Nl) {
+            const int i = __ffsll((long long)Nl) - 1;
+            Nl &= Nl - 1;
+            T h[ETA];
+            const T* left = sLeft + (size_t)(l - 1) * ETA * n;
+#pragma unroll 1
+            for (int r = 0; r < eta; ++r) {
+                T v = left[r * n + i];
+                for (int st = 0; st < nabove; ++st) {
+                    const int ls = htag[st] >> 8, is = htag[st] & 255;
+                    v = cfma(v, hs[st][r], P[(size_t)tri(ls - 1, l) * n * n + (size_t)is * n + i]);
+                }
+                h[r] = mk(R(-2) * v.x, R(-2) * v.y);
+            }
+            const T* rc = RC + ((size_t)(l - 1) * n + i) * eta;
+#pragma unroll 1
+            for (int c = 0; c < eta; ++c) {
+                const T v = rc[c];
+                for (int r = 0; r < eta; ++r) M[r][c] = cfma(M[r][c], h[r], v);
+            }
+            if (store && nst < kMaxApproxStored) {
+                for (int r = 0; r < eta; ++r) hs[nst][r] = h[r];
+                htag[nst] = (l << 8) | i;
+                ++nst;
+            }
+        }
+    }
+    // LU with partial pivoting (largest |a|^2, lowest row on ties)
+    T d = mk(R(1), R(0));
+#pragma unroll 1
+    for (int k = 0; k < eta; ++k) {
+        int p = k;
+        R best = abs2(M[k][k]);
+        for (int i = k + 1; i < eta; ++i)
+            if (abs2(M[i][k]) > best) {
+                best = abs2(M[i][k]);
+                p = i;
+            }
+        if (!(best >= min_pivot2(R(0)))) return mk(R(0), R(0));
+        if (p != k) {
+            d = mk(-d.x, -d.y);
+            for (int j = k; j < eta; ++j) {
+                const T t = M[k][j];
+                M[k][j] = M[p][j];
+                M[p][j] = t;
+            }
+        }
+        d = cmul(d, M[k][k]);
+        const R ib = R(1) / best;
+        const T ip = mk(M[k][k].x * ib, -M[k][k].y * ib);
+        for (int i = k + 1; i < eta; ++i) {
+            const T l = cmul(M[i][k], ip);
+            for (int j = k + 1; j < eta; ++j) M[i][j] = cfms(M[i][j], l, M[k][j]);
+        }
+    }
+    return d;
+}
+
+// A trajectory deferred from the main loop// A trajectory deferred from the main loop (more than three flipped pairs in
 // a block, or a block whose A0 takes the rank-one form): its flipped pairs
 // per block, the product of its sampling ratios and its flip count.
 template <typename RQ> struct Deferred {
@@ -472,7 +560,8 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
         // and the sums of D = y0 h recovered from them in FP64 once per thread.
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         float hs_r = 0.f, hc_r = 0.f, hs_i = 0.f, hc_i = 0.f, h_rr = 0.f, h_ii = 0.f, h_ri = 0.f;
-        float esum = 0.f, gsum = 0.f;  // error bounds: absolute (FP64 sums), and in units of |y0| (K form)
+        // squared per-trajectory rounding bounds: absolute (FP64 sums), and in units of |y0|^2 (K form)
+        float esum = 0.f, gsum = 0.f;
         unsigned long long nflips_tot = 0, nlu = 0, nfall = 0;
         uint64_t N[kMaxBlocks][kMaxApproxLayers];
         T hs[kMaxApproxStored][ETA];
@@ -507,10 +596,12 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
                         const T* sA0 = reinterpret_cast<const T*>(sm_raw + L.sA0[B]);
                         const T* sLeft = reinterpret_cast<const T*>(sm_raw + L.sLeft[B]);
                         T det;
+                        uint64_t Nl[kMaxApproxLayers] = {};
+                        uint32_t lf = lflag[B];
+                        const uint64_t* nl = N[B];
                         if (A.kform) {
                             // per-layer flipped modes from the flipped pairs
-                            uint64_t Nl[kMaxApproxLayers] = {};
-                            uint32_t lf = 0;
+                            lf = 0;
                             uint64_t pm = Nm[B];
                             while (pm) {
                                 const int pp = __ffsll((long long)pm) - 1;
@@ -519,9 +610,13 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
                                 Nl[(v >> 8) - 1] |= 1ull << (v & 255);
                                 lf |= 1u << ((v >> 8) - 1);
                             }
-                            det = rank_one_det<R, ETA>(A.blk[B], sA0, sLeft, lf, Nl, hs, htag, er2, zabs2);
+                            nl = Nl;
+                        }
+                        if constexpr (!kF32 && ETA > 8) {
+                            det = rank_one_det_loop<R, ETA>(A.blk[B], sA0, sLeft, lf, nl, hs, htag);
+                            er2 = zabs2 = R(0);
                         } else {
-                            det = rank_one_det<R, ETA>(A.blk[B], sA0, sLeft, lflag[B], N[B], hs, htag, er2, zabs2);
+                            det = rank_one_det<R, ETA>(A.blk[B], sA0, sLeft, lf, nl, hs, htag, er2, zabs2);
                         }
                         dd = make_double2((double)det.x, (double)det.y);
                         e = (float)sqrt(abs2(det) * er2 + zabs2);
@@ -545,7 +640,8 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
             if constexpr (kF32) {
                 const float e = A.nblocks == 2 ? eb[0] * ab[1] + eb[1] * ab[0] : eb[0];
                 // plus the FP32 rounding of rq (one per flip) and of the products
-                esum += fabsf((float)mag) * e + (float)(nflip + 4) * (float)(fabs(mag) * sqrt(dr * dr + di * di));
+                const float es = fabsf((float)mag) * e + (float)(nflip + 4) * (float)(fabs(mag) * sqrt(dr * dr + di * di));
+                esum = fmaf(es, es, esum);
             }
         };
         // a warp's deferred trajectories, one per lane
@@ -655,7 +751,8 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
                                 h_ii = fmaf(hi, hi, h_ii);
                                 h_ri = fmaf(hr, hi, h_ri);
                                 const float eg = A.nblocks == 2 ? ed[0] * ad[1] + ed[1] * ad[0] : ed[0];
-                                gsum += fabsf(rq) * eg + (float)(nflip + 4) * sqrtf(gg.x * gg.x + gg.y * gg.y);
+                                const float es = fabsf(rq) * eg + (float)(nflip + 4) * sqrtf(gg.x * gg.x + gg.y * gg.y);
+                                gsum = fmaf(es, es, gsum);
                             } else {
                                 const double2 y = cmul(make_double2(y0r, y0i), make_double2(rq * g.x, rq * g.y));
                                 const double2 Y = times_i_pow(y, nflip);
@@ -703,7 +800,7 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
             acc[2] += a2 * rr - 2.0 * ab2 * ri + b2 * ii;
             acc[3] += a2 * ii + 2.0 * ab2 * ri + b2 * rr;
             acc[4] += (a2 - b2) * ri + ab2 * (rr - ii);
-            esum += (float)sqrt(y0r * y0r + y0i * y0i) * gsum;
+            esum += (float)(y0r * y0r + y0i * y0i) * gsum;
         }
 
         // ---- deterministic CTA reduction
@@ -743,6 +840,8 @@ static cudaError_t launch_approx_eta(const ApproxDev& a, const uint64_t* bits, c
     return cudaGetLastError();
 }
 
+// Up to 13 particles per block; for the larger ones the eta x eta matrix of the
+// (deferred, rare) rank-one form partly lives in local memory.
 template <typename R>
 static cudaError_t launch_approx_r(const ApproxDev& a, const uint64_t* bits, int eta, cudaStream_t s) {
     switch (eta) {
@@ -754,27 +853,11 @@ static cudaError_t launch_approx_r(const ApproxDev& a, const uint64_t* bits, int
         case 6: return launch_approx_eta<R, 6>(a, bits, s);
         case 7: return launch_approx_eta<R, 7>(a, bits, s);
         case 8: return launch_approx_eta<R, 8>(a, bits, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-// FP32 minors up to 13 particles per block (the fallback's matrix partly lives in local memory)
-template <>
-cudaError_t launch_approx_r<float>(const ApproxDev& a, const uint64_t* bits, int eta, cudaStream_t s) {
-    switch (eta) {
-        case 1: return launch_approx_eta<float, 1>(a, bits, s);
-        case 2: return launch_approx_eta<float, 2>(a, bits, s);
-        case 3: return launch_approx_eta<float, 3>(a, bits, s);
-        case 4: return launch_approx_eta<float, 4>(a, bits, s);
-        case 5: return launch_approx_eta<float, 5>(a, bits, s);
-        case 6: return launch_approx_eta<float, 6>(a, bits, s);
-        case 7: return launch_approx_eta<float, 7>(a, bits, s);
-        case 8: return launch_approx_eta<float, 8>(a, bits, s);
-        case 9: return launch_approx_eta<float, 9>(a, bits, s);
-        case 10: return launch_approx_eta<float, 10>(a, bits, s);
-        case 11: return launch_approx_eta<float, 11>(a, bits, s);
-        case 12: return launch_approx_eta<float, 12>(a, bits, s);
-        case 13: return launch_approx_eta<float, 13>(a, bits, s);
+        case 9: return launch_approx_eta<R, 9>(a, bits, s);
+        case 10: return launch_approx_eta<R, 10>(a, bits, s);
+        case 11: return launch_approx_eta<R, 11>(a, bits, s);
+        case 12: return launch_approx_eta<R, 12>(a, bits, s);
+        case 13: return launch_approx_eta<R, 13>(a, bits, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -796,7 +879,7 @@ cudaError_t launch_approx(const ApproxDev& a, const uint64_t* bits, bool fp64, c
 
 // alpha_hat = Y0 + sum D / t; p_hat = |alpha_hat|^2;
 // stderr = 2 sqrt(Var[Re(conj(alpha_hat) Y)] / t) from the shifted sums;
-// FP32 path: |delta alpha| <= err_coef * (error sum) / t and the estimate of
+// FP32 path: |delta alpha| ~ err_coef sqrt(n_max (sum of e_s^2)) / t and the estimate of
 // the relative error of p_hat, (2 |alpha| |delta alpha| + |delta alpha|^2) / max(p_hat, p_floor).
 // Listed mode (the FP64 redo of flagged results) covers the listed bitstrings
 // and negates their error estimates.
@@ -839,7 +922,7 @@ __global__ void k_approx_finalize(ApproxDev A, double* __restrict__ out, double*
     }
     double est = 0.0;
     if (A.err_coef > 0.0) {
-        const double da = A.err_coef * s[5] / t;
+        const double da = A.err_coef * sqrt(A.nmax * s[5]) / t;
         est = (2.0 * sqrt(ph) * da + da * da) / fmax(ph, A.p_floor);
     }
     if (err) err[b] = est;
