@@ -66,9 +66,9 @@ struct ApproxSmem {
 __host__ __device__ inline ApproxSmem approx_smem(const ApproxDev& A, int eta_t, size_t csz) {
     ApproxSmem s{};
     size_t off = 0;
-    const int k4 = (A.k + 3) & ~3;
+    const int k16 = (A.k + 15) & ~15;
     s.sT = off;
-    off = al16(off + (size_t)k4 * 4);
+    off = al16(off + (size_t)k16 * 4);
     s.sGp = off;
     if (A.kform) off = al16(off + (size_t)A.nblocks * A.k * 8);
     int fmax = 0, lnmax = 0;
@@ -145,6 +145,30 @@ __device__ __forceinline__ cplx_t<R> kdet(const cplx_t<R>* __restrict__ K, int f
     R er2, zabs2;
     const T d = lu_det_regs<R, kMaxKSmall>(M, er2, zabs2);
     err = sqrt(abs2(d) * er2 + zabs2) + R(m) * cabs_<R>(d);
+    return d;
+}
+
+// det(I + K[N, N]) for |N| = 1 or 2 (the main loop's cases; no LU code), with
+// the same error bound as kdet.
+template <typename R>
+__device__ __forceinline__ cplx_t<R> kdet12(const cplx_t<R>* __restrict__ K, int f, uint64_t N, int m, R& err) {
+    using T = cplx_t<R>;
+    const int i0 = __ffsll((long long)N) - 1;
+    N &= N - 1;
+    const T kii = K[i0 * f + i0];
+    const T a = mk(R(1) + kii.x, kii.y);
+    if (m == 1) {
+        err = cabs_<R>(kii) + cabs_<R>(a);
+        return a;
+    }
+    const int i1 = __ffsll((long long)N) - 1;
+    const T kjj = K[i1 * f + i1];
+    const T b = K[i0 * f + i1], c = K[i1 * f + i0];
+    const T e = mk(R(1) + kjj.x, kjj.y);
+    const T ae = cmul(a, e), bc = cmul(b, c);
+    const T d = mk(ae.x - bc.x, ae.y - bc.y);
+    const R na = cabs_<R>(a), ne = cabs_<R>(e), nb = cabs_<R>(b), nc = cabs_<R>(c);
+    err = ne * (cabs_<R>(kii) + na) + na * (cabs_<R>(kjj) + ne) + R(3) * na * ne + R(5) * nb * nc + cabs_<R>(d);
     return d;
 }
 
@@ -332,6 +356,95 @@ template <typename RQ> struct Deferred {
     int nflip;
 };
 
+// One trajectory by the general forms, for the deferred trajectories and for
+// circuits without the K form: per block det0_B, det0_B det(I + K[N, N]) with
+// |N| <= 4, or the rank-one form with an eta x eta LU; returns D = Y - y0, the
+// FP32 rounding bound of Y and the number of rank-one minors. Kept out of
+// line: the main loop's instruction footprint stays small.
+struct GeneralTerm {
+    double Dr, Di;
+    float es;
+    int nfall;
+};
+
+template <typename R, int ETA>
+__device__ __noinline__ GeneralTerm general_term(const ApproxDev& A, unsigned char* sm_raw, const ApproxSmem& L,
+                                                 const double2* s_det0, const float* s_abs0, const int* s_bad,
+                                                 const uint32_t (&lflag)[kMaxBlocks], const uint64_t (&Nm)[kMaxBlocks],
+                                                 double rq, int nflip, double y0r, double y0i,
+                                                 const uint64_t (&N)[kMaxBlocks][kMaxApproxLayers],
+                                                 cplx_t<R> (&hs)[kMaxApproxStored][ETA],
+                                                 int (&htag)[kMaxApproxStored]) {
+    using T = cplx_t<R>;
+    constexpr bool kF32 = std::is_same<R, float>::value;
+    GeneralTerm out{0.0, 0.0, 0.f, 0};
+    double dr = 1.0, di = 0.0;
+    float eb[kMaxBlocks] = {}, ab[kMaxBlocks] = {};
+    for (int B = 0; B < A.nblocks; ++B) {
+        const float a0 = s_abs0[B];
+        float e = 0.f, a = a0;
+        double2 dd = s_det0[B];
+        const int m = __popcll(Nm[B]);
+        if (lflag[B] != 0) {
+            if (A.kform && !s_bad[B] && m <= kMaxKSmall) {
+                if (m > 0) {
+                    R err;
+                    const T d = kdet<R>(reinterpret_cast<const T*>(sm_raw + L.sK[B]), A.blk[B].f, Nm[B], m, err);
+                    dd = cmul(dd, make_double2((double)d.x, (double)d.y));
+                    e = a0 * (float)err;
+                    a = a0 * (float)cabs_<R>(d);
+                }
+            } else {
+                ++out.nfall;
+                R er2, zabs2;
+                const T* sA0 = reinterpret_cast<const T*>(sm_raw + L.sA0[B]);
+                const T* sLeft = reinterpret_cast<const T*>(sm_raw + L.sLeft[B]);
+                T det;
+                uint64_t Nl[kMaxApproxLayers] = {};
+                uint32_t lf = lflag[B];
+                const uint64_t* nl = N[B];
+                if (A.kform) {
+                    // per-layer flipped modes from the flipped pairs
+                    lf = 0;
+                    uint64_t pm = Nm[B];
+                    while (pm) {
+                        const int pp = __ffsll((long long)pm) - 1;
+                        pm &= pm - 1;
+                        const int v = A.blk[B].pair_lm[pp];
+                        Nl[(v >> 8) - 1] |= 1ull << (v & 255);
+                        lf |= 1u << ((v >> 8) - 1);
+                    }
+                    nl = Nl;
+                }
+                if constexpr (!kF32 && ETA > 8) {
+                    det = rank_one_det_loop<R, ETA>(A.blk[B], sA0, sLeft, lf, nl, hs, htag);
+                    er2 = zabs2 = R(0);
+                } else {
+                    det = rank_one_det<R, ETA>(A.blk[B], sA0, sLeft, lf, nl, hs, htag, er2, zabs2);
+                }
+                dd = make_double2((double)det.x, (double)det.y);
+                e = (float)sqrt(abs2(det) * er2 + zabs2);
+                a = (float)cabs_<R>(det);
+            }
+        }
+        if (B == 0) eb[0] = e, ab[0] = a;
+        else eb[1] = e, ab[1] = a;
+        const double t2 = dr * dd.x - di * dd.y;
+        di = dr * dd.y + di * dd.x;
+        dr = t2;
+    }
+    const double mag = A.R0 * rq;
+    const double2 Y = times_i_pow(make_double2(mag * dr, mag * di), nflip);
+    out.Dr = Y.x - y0r;
+    out.Di = Y.y - y0i;
+    if constexpr (kF32) {
+        const float e = A.nblocks == 2 ? eb[0] * ab[1] + eb[1] * ab[0] : eb[0];
+        // plus the FP32 rounding of rq (one per flip) and of the products
+        out.es = fabsf((float)mag) * e + (float)(nflip + 4) * (float)(fabs(mag) * sqrt(dr * dr + di * di));
+    }
+    return out;
+}
+
 template <typename R, int ETA>
 __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const uint64_t* __restrict__ bits) {
     using T = cplx_t<R>;
@@ -353,14 +466,14 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
 
     const int tid = threadIdx.x;
     const int k = A.k;
-    const int k4 = (k + 3) & ~3;
     const ApproxSmem L = approx_smem(A, ETA, sizeof(T));
     uint32_t* sT = reinterpret_cast<uint32_t*>(sm_raw + L.sT);
     uint64_t* sGp = reinterpret_cast<uint64_t*>(sm_raw + L.sGp);
     double2* aug = reinterpret_cast<double2*>(sm_raw + L.aug);  // [ETA][2 ETA]
     double2* lam = reinterpret_cast<double2*>(sm_raw + L.lam);  // [L][ETA][n] FP64 Lambda_l rows
     double2* yrow = reinterpret_cast<double2*>(sm_raw + L.yrow);  // [f][ETA] (rho_a A0^{-1}) rows
-    for (int j = tid; j < k4; j += NT) sT[j] = (j < k) ? A.T[j] : 0u;
+    const int k16 = (k + 15) & ~15;
+    for (int j = tid; j < k16; j += NT) sT[j] = (j < k) ? A.T[j] : 0u;
     if (A.kform)
         for (int e = tid; e < A.nblocks * k; e += NT) sGp[e] = A.gpair[e];
 
@@ -572,77 +685,16 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
         // one trajectory given its flipped modes (rank-one form where needed), added to acc
         auto add_general = [&](const uint32_t (&lflag)[kMaxBlocks], const uint64_t (&Nm)[kMaxBlocks], double rq,
                                int nflip) {
-            double dr = 1.0, di = 0.0;
-            float eb[kMaxBlocks] = {}, ab[kMaxBlocks] = {};
-            for (int B = 0; B < A.nblocks; ++B) {
-                const float a0 = s_abs0[B];
-                float e = 0.f, a = a0;
-                double2 dd = s_det0[B];
-                const int m = __popcll(Nm[B]);
-                if (lflag[B] != 0) {
-                    if (A.kform && !s_bad[B] && m <= kMaxKSmall) {
-                        if (m > 0) {
-                            R err;
-                            const T d = kdet<R>(reinterpret_cast<const T*>(sm_raw + L.sK[B]), A.blk[B].f, Nm[B], m,
-                                                err);
-                            dd = cmul(dd, make_double2((double)d.x, (double)d.y));
-                            e = a0 * (float)err;
-                            a = a0 * (float)cabs_<R>(d);
-                        }
-                    } else {
-                        ++nfall;
-                        ++nlu;
-                        R er2, zabs2;
-                        const T* sA0 = reinterpret_cast<const T*>(sm_raw + L.sA0[B]);
-                        const T* sLeft = reinterpret_cast<const T*>(sm_raw + L.sLeft[B]);
-                        T det;
-                        uint64_t Nl[kMaxApproxLayers] = {};
-                        uint32_t lf = lflag[B];
-                        const uint64_t* nl = N[B];
-                        if (A.kform) {
-                            // per-layer flipped modes from the flipped pairs
-                            lf = 0;
-                            uint64_t pm = Nm[B];
-                            while (pm) {
-                                const int pp = __ffsll((long long)pm) - 1;
-                                pm &= pm - 1;
-                                const int v = A.blk[B].pair_lm[pp];
-                                Nl[(v >> 8) - 1] |= 1ull << (v & 255);
-                                lf |= 1u << ((v >> 8) - 1);
-                            }
-                            nl = Nl;
-                        }
-                        if constexpr (!kF32 && ETA > 8) {
-                            det = rank_one_det_loop<R, ETA>(A.blk[B], sA0, sLeft, lf, nl, hs, htag);
-                            er2 = zabs2 = R(0);
-                        } else {
-                            det = rank_one_det<R, ETA>(A.blk[B], sA0, sLeft, lf, nl, hs, htag, er2, zabs2);
-                        }
-                        dd = make_double2((double)det.x, (double)det.y);
-                        e = (float)sqrt(abs2(det) * er2 + zabs2);
-                        a = (float)cabs_<R>(det);
-                    }
-                }
-                if (B == 0) eb[0] = e, ab[0] = a;
-                else eb[1] = e, ab[1] = a;
-                const double t2 = dr * dd.x - di * dd.y;
-                di = dr * dd.y + di * dd.x;
-                dr = t2;
-            }
-            const double mag = A.R0 * rq;
-            const double2 Y = times_i_pow(make_double2(mag * dr, mag * di), nflip);
-            const double Dr = Y.x - y0r, Di = Y.y - y0i;
-            acc[0] += Dr;
-            acc[1] += Di;
-            acc[2] = fma(Dr, Dr, acc[2]);
-            acc[3] = fma(Di, Di, acc[3]);
-            acc[4] = fma(Dr, Di, acc[4]);
-            if constexpr (kF32) {
-                const float e = A.nblocks == 2 ? eb[0] * ab[1] + eb[1] * ab[0] : eb[0];
-                // plus the FP32 rounding of rq (one per flip) and of the products
-                const float es = fabsf((float)mag) * e + (float)(nflip + 4) * (float)(fabs(mag) * sqrt(dr * dr + di * di));
-                esum = fmaf(es, es, esum);
-            }
+            const GeneralTerm gt = general_term<R, ETA>(A, sm_raw, L, s_det0, s_abs0, s_bad, lflag, Nm, rq, nflip,
+                                                        y0r, y0i, N, hs, htag);
+            acc[0] += gt.Dr;
+            acc[1] += gt.Di;
+            acc[2] = fma(gt.Dr, gt.Dr, acc[2]);
+            acc[3] = fma(gt.Di, gt.Di, acc[3]);
+            acc[4] = fma(gt.Dr, gt.Di, acc[4]);
+            esum = fmaf(gt.es, gt.es, esum);
+            nlu += gt.nfall;
+            nfall += gt.nfall;
         };
         // a warp's deferred trajectories, one per lane
         auto drain = [&](int cnt) {
@@ -670,33 +722,50 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
                 RQ rq = RQ(1);
                 uint32_t lflag[kMaxBlocks] = {};
                 uint64_t Nm[kMaxBlocks] = {};
-                for (int q4 = 0; q4 < k4 / 4; ++q4) {
-                    const uint4 u = philox4x32_10(make_uint4((uint32_t)q4, (uint32_t)s, blo, bhi), A.key0, A.key1);
+                // gate j flipped: its ratio and its flips (layer, modes; pairs for the K form)
+                auto flip = [&](int j) {
+                    ++nflip;
+                    if constexpr (kF32) rq *= A.qratio32[j];
+                    else rq *= A.qratio[j];
+#pragma unroll
+                    for (int B = 0; B < kMaxBlocks; ++B) {
+                        if (B >= A.nblocks) break;
+                        const int l = A.glayer[B * k + j];
+                        if (l) {
+                            const uint32_t bit = 1u << (l - 1);
+                            if (A.kform) {
+                                Nm[B] ^= sGp[B * k + j];
+                            } else {  // per-layer flipped modes for the rank-one form
+                                if (!(lflag[B] & bit)) N[B][l - 1] = 0;
+                                N[B][l - 1] ^= A.gmodes[B * k + j];
+                            }
+                            lflag[B] |= bit;
+                        }
+                    }
+                };
+                auto hits = [&](const uint4 u, int q4) {
                     const uint4 th = *reinterpret_cast<const uint4*>(sT + 4 * q4);
-                    uint32_t hit = (uint32_t)(u.x < th.x) | ((uint32_t)(u.y < th.y) << 1) |
-                                   ((uint32_t)(u.z < th.z) << 2) | ((uint32_t)(u.w < th.w) << 3);
+                    return (uint32_t)(u.x < th.x) | ((uint32_t)(u.y < th.y) << 1) | ((uint32_t)(u.z < th.z) << 2) |
+                           ((uint32_t)(u.w < th.w) << 3);
+                };
+                // four independent Philox blocks at a time (instruction-level parallelism
+                // for a chain of dependent multiplies), then their 16 gates' flips in order;
+                // the thresholds are padded with zeros to a multiple of 16 gates (no flips)
+                const int nq = k16 / 4;
+                for (int q4 = 0; q4 < nq; q4 += 4) {
+                    const uint4 u0 = philox4x32_10(make_uint4((uint32_t)q4, (uint32_t)s, blo, bhi), A.key0, A.key1);
+                    const uint4 u1 =
+                        philox4x32_10(make_uint4((uint32_t)q4 + 1u, (uint32_t)s, blo, bhi), A.key0, A.key1);
+                    const uint4 u2 =
+                        philox4x32_10(make_uint4((uint32_t)q4 + 2u, (uint32_t)s, blo, bhi), A.key0, A.key1);
+                    const uint4 u3 =
+                        philox4x32_10(make_uint4((uint32_t)q4 + 3u, (uint32_t)s, blo, bhi), A.key0, A.key1);
+                    uint32_t hit = hits(u0, q4) | (hits(u1, q4 + 1) << 4) | (hits(u2, q4 + 2) << 8) |
+                                   (hits(u3, q4 + 3) << 12);
                     while (hit) {
                         const int w = __ffs(hit) - 1;
                         hit &= hit - 1;
-                        const int j = 4 * q4 + w;
-                        ++nflip;
-                        if constexpr (kF32) rq *= A.qratio32[j];
-                        else rq *= A.qratio[j];
-#pragma unroll
-                        for (int B = 0; B < kMaxBlocks; ++B) {
-                            if (B >= A.nblocks) break;
-                            const int l = A.glayer[B * k + j];
-                            if (l) {
-                                const uint32_t bit = 1u << (l - 1);
-                                if (A.kform) {
-                                    Nm[B] ^= sGp[B * k + j];
-                                } else {  // per-layer flipped modes for the rank-one form
-                                    if (!(lflag[B] & bit)) N[B][l - 1] = 0;
-                                    N[B][l - 1] ^= A.gmodes[B * k + j];
-                                }
-                                lflag[B] |= bit;
-                            }
-                        }
+                        flip(4 * q4 + w);
                     }
                 }
                 nflips_tot += nflip;
@@ -721,7 +790,7 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
                                 const T* Kb = reinterpret_cast<const T*>(sm_raw + L.sK[B]);
                                 R err;
                                 const T d = m == 3 ? kdet3<R>(Kb, A.blk[B].f, Nm[B], err)
-                                                   : kdet<R>(Kb, A.blk[B].f, Nm[B], m, err);
+                                                   : kdet12<R>(Kb, A.blk[B].f, Nm[B], m, err);
                                 g = cmul(g, d);
                                 ed[B] = err;
                                 ad[B] = cabs_<R>(d);
