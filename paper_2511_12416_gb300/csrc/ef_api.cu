@@ -134,11 +134,11 @@ struct HostBlock {
     std::vector<cd> RC;  // L x n x eta
     std::vector<int> pair_lm;  // flippable (layer, mode) pairs, layer-major: layer << 8 | local mode
     // device
-    DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dOmegaHatFF, dSh, dPerm, dGoff, dInvOff, dInvXs, dM64, dM32, dD32, dD64, dMlist,
+    DBuf dS0C, dT, dF, dOmega, dOmega32, dOmegaHat, dOmegaHatFF, dSh, dPerm, dGoff, dInvOff, dInvXs, dM64, dM32, dD32, dE32, dD64, dMlist,
         dP64, dP32, dRC64, dRC32, dCols, dPairLM;
     DBuf dCot, dEbar, dTbar, dSbar, dSumT, dSumS, dSumE;
     template <typename F> void for_each_buf(F f) {
-        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dOmegaHatFF, &dSh, &dPerm, &dGoff, &dInvOff, &dInvXs, &dM64, &dM32, &dD32, &dD64, &dMlist, &dP64, &dP32, &dRC64,
+        for (DBuf* b : {&dS0C, &dT, &dF, &dOmega, &dOmega32, &dOmegaHat, &dOmegaHatFF, &dSh, &dPerm, &dGoff, &dInvOff, &dInvXs, &dM64, &dM32, &dD32, &dE32, &dD64, &dMlist, &dP64, &dP32, &dRC64,
                         &dRC32, &dCols, &dPairLM, &dCot, &dEbar, &dTbar, &dSbar, &dSumT, &dSumS, &dSumE})
             f(*b);
     }
@@ -891,11 +891,13 @@ bool per_minor_recompute(const ef_circuit* c) {
     return minors <= 8192;
 }
 
-// Bytes per (pattern, bitstring) determinant: FP32 results (float4) unless
-// FP64-only, FP64 ones (double2) for FP64 and for the recomputes of AUTO.
+// Bytes per (pattern, bitstring) determinant: FP32 results (float2 value and
+// a 16-bit error term) unless FP64-only, FP64 ones (double2) for FP64 and for
+// the recomputes of AUTO.
 size_t det_bytes(const ef_circuit* c) {
     const int p = c->opt.precision;
-    return (p != EF_PREC_FP64 ? sizeof(float4) : 0) + (p != EF_PREC_FP32_MINOR ? sizeof(double2) : 0);
+    return (p != EF_PREC_FP64 ? sizeof(float2) + sizeof(uint16_t) : 0) +
+           (p != EF_PREC_FP32_MINOR ? sizeof(double2) : 0);
 }
 
 // Bitstrings per batch so that the per-(pattern, bitstring) determinants stay
@@ -958,6 +960,7 @@ ef::ExactCombineDev make_combine(const ef_circuit* c, const ExactBuffers& eb) {
         cm.r[b] = c->blk[b].r;
         cm.r_loc[b] = c->blk[b].r_loc;
         cm.D32[b] = eb.blk[b].D32;
+        cm.E32[b] = eb.blk[b].E32;
         cm.D64[b] = eb.blk[b].D64;
         cm.OmegaHatDF[b] = eb.OmegaHatFF[b];
         cm.Omega[b] = eb.Omega[b];
@@ -1143,7 +1146,8 @@ int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
         EF_CK(B.dM64.ensure(ny * ne * sizeof(double2)));
         if (!fp64_only) EF_CK(B.dM32.ensure(ny * ne * sizeof(float2)));
         const bool d32 = c->opt.precision != EF_PREC_FP64, d64 = c->opt.precision != EF_PREC_FP32_MINOR;
-        if (d32) EF_CK(B.dD32.ensure(ny * (size_t)cap * sizeof(float4)));
+        if (d32) EF_CK(B.dD32.ensure(ny * (size_t)cap * sizeof(float2)));
+        if (d32) EF_CK(B.dE32.ensure(ny * (size_t)cap * sizeof(uint16_t)));
         if (d64) EF_CK(B.dD64.ensure(ny * (size_t)cap * sizeof(double2)));
         ef::ExactBlockDev& d = eb.blk[b];
         exact_block_geometry(c, b, cap, d);
@@ -1152,7 +1156,8 @@ int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
         d.F = B.dF.as<uint32_t>();
         d.M64 = B.dM64.as<double2>();
         d.M32 = fp64_only ? nullptr : B.dM32.as<float2>();
-        d.D32 = d32 ? B.dD32.as<float4>() : nullptr;
+        d.D32 = d32 ? B.dD32.as<float2>() : nullptr;
+        d.E32 = d32 ? B.dE32.as<uint16_t>() : nullptr;
         d.D64 = d64 ? B.dD64.as<double2>() : nullptr;
         eb.Omega[b] = B.dOmega.as<double2>();
         eb.Omega32[b] = B.dOmega32.as<float2>();
@@ -1388,6 +1393,7 @@ int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_
         d.M64 = B.dM64.as<double2>();
         d.M32 = nullptr;
         d.D32 = nullptr;
+        d.E32 = nullptr;
         d.D64 = B.dD64.as<double2>();
         cm.mask[b][0] = B.mask[0];
         cm.mask[b][1] = B.mask[1];
@@ -2119,7 +2125,8 @@ size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* bas
         ef::ExactBlockDev& d = eb.blk[b];
         d.M64 = cv.take<double2>(ny * ne);
         d.M32 = want32 ? cv.take<float2>(ny * ne) : nullptr;
-        d.D32 = c->opt.precision != EF_PREC_FP64 ? cv.take<float4>(ny * (size_t)eb.cap) : nullptr;
+        d.D32 = c->opt.precision != EF_PREC_FP64 ? cv.take<float2>(ny * (size_t)eb.cap) : nullptr;
+        d.E32 = c->opt.precision != EF_PREC_FP64 ? cv.take<uint16_t>(ny * (size_t)eb.cap) : nullptr;
         d.D64 = c->opt.precision != EF_PREC_FP32_MINOR ? cv.take<double2>(ny * (size_t)eb.cap) : nullptr;
     }
     eb.list = cv.take<int>((size_t)eb.cap);

@@ -65,6 +65,26 @@ template <typename R> __device__ __forceinline__ R pivot_err_term(R t) {
     return t > R(1.0 / 256) * inv_u2(R(0)) ? fmax(t, inv_u2(R(0))) : t;
 }
 
+// Stored error term of an FP32 minor: |det|^2 er2 + zabs2 (the absolute
+// squared rounding error of the determinant, units of u^2) as a bfloat16
+// rounded up, so the stored bound is never below the computed one (at most
+// 2^-7 above it). An infinite or undefined term (0 x inf after a vanishing
+// pivot) is taken as the largest float, an error too large to bound. The sign
+// bit is never set here: a set sign bit (kErrRedone) marks a determinant whose
+// value was redone in FP64.
+__device__ __forceinline__ uint16_t err_term_code(float2 det, float er2, float zabs2) {
+    float t = fmaf(fmaf(det.x, det.x, det.y * det.y), er2, zabs2);
+    t = t <= 3.0e38f ? t : 3.0e38f;
+    const uint32_t u = __float_as_uint(t) & 0x7fffffffu;
+    return (uint16_t)((u >> 16) + ((u & 0xffffu) ? 1u : 0u));
+}
+constexpr uint16_t kErrRedone = 0xbf80u;  // -1 as a bfloat16
+__device__ __forceinline__ bool err_redone(uint16_t e) { return (e & 0x8000u) != 0u; }
+// the error term (0 for a determinant redone in FP64)
+__device__ __forceinline__ float err_term_value(uint16_t e) {
+    return err_redone(e) ? 0.f : __uint_as_float((uint32_t)e << 16);
+}
+
 // multiply by i^ph (ph in 0..3)
 __device__ __forceinline__ double2 times_i_pow(double2 a, int ph) {
     switch (ph & 3) {

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const ui
 
 // Thread <-> one listed determinant (bitstring column, pattern z): redone in
 // FP64, stored in its D64 slot as a float pair (re hi, re lo, im hi, im lo),
-// and marked in D32 (er2 = -1). One launch covers the lists of nblk blocks of
+// and marked in E32 (kErrRedone). One launch covers the lists of nblk blocks of
 // the same particle count (items of block 1 follow those of block 0): the
 // run time is set by one warp's serial FP64 instruction stream, so a second
 // launch would double it.
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B0, ExactBl
         const float xh = (float)res.x, yh = (float)res.y;
         reinterpret_cast<float4*>(B.D64)[dix(pos, (uint32_t)z, B.r)] =
             make_float4(xh, (float)(res.x - (double)xh), yh, (float)(res.y - (double)yh));
-        B.D32[dix(pos, (uint32_t)z, B.r)] = make_float4(0.f, 0.f, -1.f, 0.f);
+        B.E32[dix(pos, (uint32_t)z, B.r)] = kErrRedone;
     }
 }
 
@@ -282,9 +282,11 @@ __global__ void __launch_bounds__(256) k_exact_lu_rows(ExactBlockDev B, const ui
             if (valid && r == 0) {
                 if constexpr (std::is_same<R, double>::value)
                     B.D64[dix(pos, (uint32_t)z, B.r)] = ok ? det : make_double2(0.0, 0.0);
-                else
-                    B.D32[dix(pos, (uint32_t)z, B.r)] = ok ? make_float4(det.x, det.y, er2, zabs2)
-                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                else {
+                    const size_t o = dix(pos, (uint32_t)z, B.r);
+                    B.D32[o] = ok ? det : make_float2(0.f, 0.f);
+                    B.E32[o] = ok ? err_term_code(det, er2, zabs2) : (uint16_t)0;
+                }
             }
         }
     }
@@ -456,23 +458,16 @@ __device__ __forceinline__ double neg_abs_int(double x) {
 // pair (re hi, re lo, im hi, im lo) in its D64 slot.
 __device__ __forceinline__ double2 det_at(const ExactCombineDev& C, int B, size_t idx) {
     if (C.src == 1) return C.D64[B][idx];
-    const float4 v = C.D32[B][idx];
-    if (C.src == 2 && v.z < 0.f) {
+    if (C.src == 2 && err_redone(C.E32[B][idx])) {
         const float4 f = reinterpret_cast<const float4*>(C.D64[B])[idx];
         return make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
     }
+    const float2 v = C.D32[B][idx];
     return make_double2((double)v.x, (double)v.y);
 }
-// |det|^2 er2 + zabs2 of an FP32 determinant (0 for one redone in FP64); an
-// infinite or undefined term (0 x inf after a vanishing pivot) is taken as the
-// largest float, an error too large to bound
-__device__ __forceinline__ float err_term_v(float4 v) {
-    if (v.z < 0.f) return 0.f;
-    const float t = fmaf(fmaf(v.x, v.x, v.y * v.y), v.z, v.w);
-    return t <= 3.0e38f ? t : 3.0e38f;
-}
+// the stored error term of an FP32 determinant (0 for one redone in FP64)
 __device__ __forceinline__ float err_term(const ExactCombineDev& C, int B, size_t idx) {
-    return err_term_v(C.D32[B][idx]);
+    return err_term_value(C.E32[B][idx]);
 }
 
 // Butterfly over lane bit j of a value held one per lane: the lane whose
@@ -611,7 +606,7 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
                 float4* GB = B ? G1 : G0;
                 const int nz = 1 << C.r[B];
                 for (int z = tid; z < nz; z += NT) {
-                    const float4 v = C.D32[B][dix(col, (uint32_t)z, C.r[B])];
+                    const float2 v = C.D32[B][dix(col, (uint32_t)z, C.r[B])];
                     GB[z] = make_float4(v.x, 0.f, v.y, 0.f);
                 }
             }
@@ -857,10 +852,11 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
                 const int e = tid + NT * i;
                 if (e >= nz) break;
                 const size_t idx = dix(col, (uint32_t)e, C.r[B]);
-                const float4 d = C.D32[B][idx];
-                errt[B][i] = want_err ? err_term_v(d) : 0.f;
+                const float2 d = C.D32[B][idx];
+                const uint16_t ec = C.E32[B][idx];
+                errt[B][i] = want_err ? err_term_value(ec) : 0.f;
                 float4 v = make_float4(d.x, 0.f, d.y, 0.f);
-                if (C.src == 2 && d.z < 0.f)  // redone in FP64, stored as a float pair
+                if (C.src == 2 && err_redone(ec))  // redone in FP64, stored as a float pair
                     v = reinterpret_cast<const float4*>(C.D64[B])[idx];
                 for (int pass = 0; pass < 2; ++pass)
                     for (int j = 0; j < rl; ++j) {
@@ -1077,10 +1073,11 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 const size_t idx = dix(col, (uint32_t)(z0 | l), C.r[B]);
-                const float4 d = C.D32[B][idx];
-                errt[rr][l] = want_err ? err_term_v(d) : 0.f;
+                const float2 d = C.D32[B][idx];
+                const uint16_t ec = C.E32[B][idx];
+                errt[rr][l] = want_err ? err_term_value(ec) : 0.f;
                 v[l] = make_float4(d.x, 0.f, d.y, 0.f);
-                if (C.src == 2 && d.z < 0.f)  // redone in FP64, stored as a float pair
+                if (C.src == 2 && err_redone(ec))  // redone in FP64, stored as a float pair
                     v[l] = reinterpret_cast<const float4*>(C.D64[B])[idx];
             }
             row_wht<RL>(v, cf_add, cf_sub);

@@ -41,12 +41,14 @@ struct ExactBlockDev {
     double2* M64;           // 2^r x n x eta branch matrices (FP64)
     float2* M32;            // same, FP32 (may be null)
     // determinants per (bitstring column, pattern), [stride][2^r] each (dix):
-    float4* D32;            // FP32 LU: (det re, det im, er2, zabs2); er2 < 0 marks one redone in D64
+    float2* D32;            // FP32 LU: det
+    uint16_t* E32;          // FP32 LU: error term |det|^2 er2 + zabs2 as bfloat16 rounded up;
+                            // the sign bit set marks a determinant redone in D64
     double2* D64;           // FP64 LU: det
 };
 
 // Index of the determinant of pattern z (of 2^r) for bitstring column col in
-// D32 / D64: bitstring-major, so one bitstring's 2^r determinants are
+// D32 / E32 / D64: bitstring-major, so one bitstring's 2^r determinants are
 // contiguous (coalesced reads by the combine; the LU's threads each write a
 // run of consecutive patterns).
 __host__ __device__ inline size_t dix(int64_t col, uint32_t z, int r) { return ((size_t)col << r) + z; }
@@ -60,7 +62,8 @@ struct ExactCombineDev {
     uint64_t mask[kMaxBlocks][2];
     int eta[kMaxBlocks];
     int r[kMaxBlocks], r_loc[kMaxBlocks];
-    const float4* D32[kMaxBlocks];
+    const float2* D32[kMaxBlocks];
+    const uint16_t* E32[kMaxBlocks];
     const double2* D64[kMaxBlocks];
     int src;                           // determinants from D32 (0), D64 (1), D32 with D64 where marked (2)
     const double2* Omega[kMaxBlocks];  // 2^r_loc pattern weights of the local gates

@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B0, ExactBlo
         if (b >= nb) continue;
         for (int t = 0; t < Y; ++t) {
             const size_t z = (size_t)chunk * Y + t;
-            float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 det = make_float2(0.f, 0.f);
+            uint16_t ec = 0;
             if (ok) {
                 const float2* Mt = smM + (size_t)t * n * S;
                 float2 A[ETA][ETA];
@@ -62,10 +63,12 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B0, ExactBlo
                     for (int j = 0; j < ETA; ++j) A[i][j] = rp[j];
                 }
                 float er2, zabs2;
-                const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
-                res = make_float4(det.x, det.y, er2, zabs2);
+                det = lu_det_regs<float, ETA>(A, er2, zabs2);
+                ec = err_term_code(det, er2, zabs2);
             }
-            B.D32[dix(b, (uint32_t)z, B.r)] = res;
+            const size_t o = dix(b, (uint32_t)z, B.r);
+            B.D32[o] = det;
+            B.E32[o] = ec;
         }
     }
 }
@@ -155,7 +158,8 @@ __global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restri
             const bool ok = decode_rows<ETA>(E.bits[2 * b], E.bits[2 * b + 1], B.mask0, B.mask1, rows);
             for (int t = 0; t < Y; ++t) {
                 const size_t z = (size_t)chunk * Y + t;
-                float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 det = make_float2(0.f, 0.f);
+                uint16_t ec = 0;
                 if (ok) {
                     const float2* Mt = smQ + (size_t)t * n * S;
                     float2 A[ETA][ETA];
@@ -166,10 +170,12 @@ __global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restri
                         for (int j = 0; j < ETA; ++j) A[i][j] = rp[j];
                     }
                     float er2, zabs2;
-                    const float2 det = lu_det_regs<float, ETA>(A, er2, zabs2);
-                    res = make_float4(det.x, det.y, er2, zabs2);
+                    det = lu_det_regs<float, ETA>(A, er2, zabs2);
+                    ec = err_term_code(det, er2, zabs2);
                 }
-                B.D32[dix(b, (uint32_t)z, B.r)] = res;
+                const size_t o = dix(b, (uint32_t)z, B.r);
+                B.D32[o] = det;
+                B.E32[o] = ec;
             }
         }
         __syncthreads();
