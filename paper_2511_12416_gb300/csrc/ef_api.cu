@@ -1466,6 +1466,7 @@ ef::ApproxDev approx_dev_for(const ef_circuit* c, const ef::ApproxDev& base, boo
     const int eta_t = ef::approx_eta_template(a);
     if (a.kform && ef::approx_smem_bytes(a, eta_t, fp64) > (size_t)200 * 1024) a.kform = 0;
     a.err_coef = fp64 ? 0.0 : base.err_coef;
+    a.err_lin = fp64 ? 0.0 : base.err_lin;
     return a;
 }
 
@@ -1510,11 +1511,22 @@ int approx_setup(ef_circuit* c, int64_t nb, int64_t t, uint64_t seed, uint64_t b
     // K u, the per-trajectory bounds being in units of u = 2^-24. Calibrated
     // against FP64 on the same trajectories (eight circuits, 12,226 results: the
     // 52-qubit LUCJ workload, the parity-test circuits, Raw Estimate circuits of
-    // the 64-circuit batch): the largest observed error / estimate is 0.028 at
-    // K = 4; K = 0.5 keeps it at 0.22.
+    // the 64-circuit batch): the largest observed error / estimate was 0.22 at
+    // K = 0.5 with n_max taken from the most probable flipped trajectory. With
+    // the pair-based n_max below and the rank-one form's bounds summed
+    // linearly, the largest ratio over the 26 Raw Estimate circuits of that
+    // batch (69,727 results) is 0.45.
     a.err_coef = 0.5 * std::ldexp(1.0, -24);
-    // the most probable flipped trajectory: x* with x_j = [pT1_j > 1/2] if it
-    // flips a gate, else the single flip with the largest pT1/pT0 added to x = 0
+    a.err_lin = std::ldexp(1.0, -24);
+    // How many trajectories share one rounded quantity: a small determinant
+    // (its flipped pairs), an entry of K (every trajectory flipping its pair),
+    // a whole trajectory. Each count is at most that of trajectories flipping
+    // one given pair, so the largest probability that a pair is flipped
+    // bounds them all: pair a of block B flips when an odd number of the gates
+    // that flip it do, P = (1 - prod_j (1 - 2 pT1_j)) / 2. Without the K form
+    // (no pair tables) the most probable flipped trajectory is used instead:
+    // x* with x_j = [pT1_j > 1/2] if it flips a gate, else the single flip
+    // with the largest pT1/pT0 added to x = 0.
     {
         double logp = 0.0, best_ratio = 0.0;
         bool any = false;
@@ -1523,13 +1535,27 @@ int approx_setup(ef_circuit* c, int64_t nb, int64_t t, uint64_t seed, uint64_t b
             logp += std::log(std::max(cp.pT1, cp.pT0));
             if (cp.pT1 <= 0.5 && cp.pT0 > 0.0) best_ratio = std::max(best_ratio, cp.pT1 / cp.pT0);
         }
-        const double q = any ? std::exp(logp) : std::exp(logp) * best_ratio;
+        double q = any ? std::exp(logp) : std::exp(logp) * best_ratio;
+        if (c->kform_ok) {
+            const int k = (int)c->cps.size();
+            for (int b = 0; b < c->nblocks; ++b)
+                for (int pp = 0; pp < 64; ++pp) {
+                    double even = 1.0;  // prod_j (1 - 2 pT1_j) over the gates flipping pair pp
+                    bool touched = false;
+                    for (int jj = 0; jj < k; ++jj)
+                        if ((c->agpair[(size_t)b * k + jj] >> pp) & 1ull) {
+                            even *= 1.0 - 2.0 * c->cps[jj].pT1;
+                            touched = true;
+                        }
+                    if (touched) q = std::max(q, 0.5 * (1.0 - even));
+                }
+        }
         const double mean = (double)t * q;
         a.nmax = std::max(1.0, mean + 3.0 * std::sqrt(mean) + 1.0);
     }
     a.tol = c->opt.tol;
     a.p_floor = c->p_floor;
-    EF_CK(c->daPart.ensure((size_t)std::max<int64_t>(nb, 1) * a.n_chunks * 10 * sizeof(double)));
+    EF_CK(c->daPart.ensure((size_t)std::max<int64_t>(nb, 1) * a.n_chunks * ef::kApproxPartStride * sizeof(double)));
     EF_CK(c->dCounters.ensure(8 * sizeof(unsigned long long)));
     EF_CK(c->daList.ensure(((size_t)std::max<int64_t>(nb, 1) + 4) * sizeof(int)));
     a.part = c->daPart.as<double>();

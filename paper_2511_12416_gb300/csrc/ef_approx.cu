@@ -31,13 +31,19 @@
 // FP32 error estimate: K is rounded to FP32 and the small determinants are
 // formed in FP32; every flipped trajectory s has a first-order bound e_s of its
 // rounding error (units of u = 2^-24: the closed forms' input and operation
-// roundings, or the LU's pivot proxy). The errors of distinct trajectories
-// are independent roundings, those of repeats of one trajectory are equal, so
-// the error of alpha_hat is estimated as K u sqrt(n_max sum_s e_s^2) / t with
-// n_max an upper estimate of any flipped trajectory's multiplicity (computed
-// on the host from the most probable flipped trajectory) and K = 0.5
-// (calibrated against FP64 on the same trajectories); the finalisation turns
-// it into an estimate of the relative error of p_hat.
+// roundings, or the LU's pivot proxy). For the K form the roundings of
+// distinct small determinants are treated as independent and those of one
+// determinant's repeats as equal, so that part of the error of alpha_hat is
+// estimated as K u sqrt(n_max sum_s e_s^2) / t, with n_max an upper estimate
+// of how many of the t trajectories share one rounded quantity (computed on
+// the host from the largest probability that a given flippable pair is
+// flipped) and K = 0.5 (calibrated against FP64 on the same trajectories).
+// Trajectories through the rank-one form all start from the same FP32 copy of
+// A0 and of its update vectors, so their input roundings add up coherently
+// (measured: an ill-conditioned A0 of a 12-mode circuit left the FP32 result
+// 2.7x its square-root estimate); their bounds are summed linearly,
+// u sum_s e_s / t, a first-order worst case. The finalisation turns the sum
+// of the two into an estimate of the relative error of p_hat.
 // det A0 is FP64, so trajectories without flips carry no error.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -52,7 +58,7 @@ namespace ef {
 
 __host__ __device__ __forceinline__ int tri(int a, int b) { return a * (a + 1) / 2 + b; }
 
-constexpr int kPartStride = 10;  // per (bitstring, chunk): 5 sums, y0 (2), valid, error sum, fallback count
+constexpr int kPartStride = kApproxPartStride;  // per (bitstring, chunk): 5 sums, y0 (2), valid, error sums (2), fallback count
 constexpr int kApproxThreads = 128;
 constexpr int kMaxKSmall = 4;    // largest |N| evaluated through K
 
@@ -445,8 +451,21 @@ __device__ __noinline__ GeneralTerm general_term(const ApproxDev& A, unsigned ch
     return out;
 }
 
+// Resident CTAs per SM the register allocation targets, per instance. Left
+// free, the compiler gave the FP32 kernel for five particles 220 registers
+// (two CTAs per SM, 5 % slower on the 52-qubit LUCJ workload than at 168);
+// the values pin the allocations measured before: FP32 4 / 3 / 2 (255
+// registers) CTAs for 1 / 2-5 / 6-13 particles, FP64 3 / 2 / 4 for 1-3 /
+// 4-8 / 9-13 (a cap of 3 for the FP32 6-13 kernels made the 64-circuit batch
+// 11 % slower).
 template <typename R, int ETA>
-__global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const uint64_t* __restrict__ bits) {
+constexpr int approx_min_ctas() {
+    return std::is_same<R, float>::value ? (ETA == 1 ? 4 : ETA <= 5 ? 3 : 1) : (ETA <= 3 ? 3 : ETA <= 8 ? 1 : 4);
+}
+
+template <typename R, int ETA>
+__global__ void __launch_bounds__(kApproxThreads, approx_min_ctas<R, ETA>())
+    k_approx(ApproxDev A, const uint64_t* __restrict__ bits) {
     using T = cplx_t<R>;
     constexpr bool kF32 = std::is_same<R, float>::value;
     using RQ = typename std::conditional<kF32, float, double>::type;
@@ -454,7 +473,7 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
     constexpr int NT = kApproxThreads;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     __shared__ DQ sQ[(NT / 32) * 64];  // per warp: deferred trajectories (at most 63 waiting)
-    __shared__ double red[6][NT];
+    __shared__ double red[7][NT];
     __shared__ unsigned long long cnt_red[3];
     __shared__ int s_rows[kMaxBlocks][ETA];
     __shared__ double2 s_det0[kMaxBlocks];
@@ -673,8 +692,9 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
         // and the sums of D = y0 h recovered from them in FP64 once per thread.
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         float hs_r = 0.f, hc_r = 0.f, hs_i = 0.f, hc_i = 0.f, h_rr = 0.f, h_ii = 0.f, h_ri = 0.f;
-        // squared per-trajectory rounding bounds: absolute (FP64 sums), and in units of |y0|^2 (K form)
-        float esum = 0.f, gsum = 0.f;
+        // per-trajectory rounding bounds: squared, absolute (deferred K-form trajectories) and in
+        // units of |y0|^2 (K form inline); linear for the rank-one form (elin)
+        float esum = 0.f, gsum = 0.f, elin = 0.f;
         unsigned long long nflips_tot = 0, nlu = 0, nfall = 0;
         uint64_t N[kMaxBlocks][kMaxApproxLayers];
         T hs[kMaxApproxStored][ETA];
@@ -692,7 +712,8 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
             acc[2] = fma(gt.Dr, gt.Dr, acc[2]);
             acc[3] = fma(gt.Di, gt.Di, acc[3]);
             acc[4] = fma(gt.Dr, gt.Di, acc[4]);
-            esum = fmaf(gt.es, gt.es, esum);
+            if (gt.nfall) elin += gt.es;
+            else esum = fmaf(gt.es, gt.es, esum);
             nlu += gt.nfall;
             nfall += gt.nfall;
         };
@@ -875,11 +896,12 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
         // ---- deterministic CTA reduction
         for (int e = 0; e < 5; ++e) red[e][tid] = acc[e];
         red[5][tid] = (double)esum;
+        red[6][tid] = (double)elin;
         if (tid == 0) cnt_red[0] = cnt_red[1] = cnt_red[2] = 0ull;
         __syncthreads();
         for (int off = NT / 2; off > 0; off >>= 1) {
             if (tid < off)
-                for (int e = 0; e < 6; ++e) red[e][tid] += red[e][tid + off];
+                for (int e = 0; e < 7; ++e) red[e][tid] += red[e][tid + off];
             __syncthreads();
         }
         atomicAdd(&cnt_red[0], nflips_tot);
@@ -893,6 +915,7 @@ __global__ void __launch_bounds__(kApproxThreads) k_approx(ApproxDev A, const ui
             outp[7] = 1.0;
             outp[8] = red[5][0];
             outp[9] = (double)cnt_red[2];
+            outp[10] = red[6][0];
             atomicAdd(&A.counters[0], cnt_red[0]);
             atomicAdd(&A.counters[1], cnt_red[1] + (unsigned long long)A.nblocks);
             atomicAdd(&A.counters[2], cnt_red[2]);
@@ -948,7 +971,8 @@ cudaError_t launch_approx(const ApproxDev& a, const uint64_t* bits, bool fp64, c
 
 // alpha_hat = Y0 + sum D / t; p_hat = |alpha_hat|^2;
 // stderr = 2 sqrt(Var[Re(conj(alpha_hat) Y)] / t) from the shifted sums;
-// FP32 path: |delta alpha| ~ err_coef sqrt(n_max (sum of e_s^2)) / t and the estimate of
+// FP32 path: |delta alpha| ~ (err_coef sqrt(n_max (sum of e_s^2)) + err_lin (sum of the
+// rank-one form's e_s)) / t and the estimate of
 // the relative error of p_hat, (2 |alpha| |delta alpha| + |delta alpha|^2) / max(p_hat, p_floor).
 // Listed mode (the FP64 redo of flagged results) covers the listed bitstrings
 // and negates their error estimates.
@@ -966,10 +990,11 @@ __global__ void k_approx_finalize(ApproxDev A, double* __restrict__ out, double*
         if (err) err[b] = 0.0;
         return;
     }
-    double s[6] = {0, 0, 0, 0, 0, 0};
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int c = 0; c < A.n_chunks; ++c) {
         for (int e = 0; e < 5; ++e) s[e] += p[(size_t)c * kPartStride + e];
         s[5] += p[(size_t)c * kPartStride + 8];
+        s[6] += p[(size_t)c * kPartStride + 10];
     }
     const double t = (double)A.t;
     const double ar = p[5] + s[0] / t, ai = p[6] + s[1] / t;
@@ -991,7 +1016,7 @@ __global__ void k_approx_finalize(ApproxDev A, double* __restrict__ out, double*
     }
     double est = 0.0;
     if (A.err_coef > 0.0) {
-        const double da = A.err_coef * sqrt(A.nmax * s[5]) / t;
+        const double da = (A.err_coef * sqrt(A.nmax * s[5]) + A.err_lin * s[6]) / t;
         est = (2.0 * sqrt(ph) * da + da * da) / fmax(ph, A.p_floor);
     }
     if (err) err[b] = est;

@@ -13,6 +13,7 @@ constexpr int kMaxEtaRows = 32;    // warp-row LU: one lane per minor row
 constexpr int kMaxEtaThread = 10;  // FP32 thread-per-minor LU (registers)
 constexpr int kMaxApproxEta = 13;    // Raw Estimate, thread per trajectory, FP32 minors
 constexpr int kMaxApproxEta64 = 13;  // FP64 minors
+constexpr int kApproxPartStride = 11; // Raw Estimate partial sums per (bitstring, trajectory chunk)
 constexpr int kMaxApproxLayers = 8;
 constexpr int kMaxApproxStored = 64;  // rank-one columns kept per trajectory
 constexpr int kMaxExactPatternBits = 22;  // 2^22 flip patterns per block
@@ -134,9 +135,10 @@ struct ApproxDev {
     int kform;               // 1: trajectory minors through K (every block has <= 64 flippable pairs)
     double kappa_max;        // A0 with ||A0||_1 ||A0^-1||_1 above this takes the rank-one form
     double err_coef;         // FP32 error estimate: K u32 (0: no estimate)
-    double nmax;             // upper estimate of a flipped trajectory's multiplicity among the t
+    double err_lin;          // FP32 error estimate, rank-one form: u32 (0: no estimate)
+    double nmax;             // upper estimate of how many of the t trajectories share one rounded quantity
     double tol, p_floor;     // EF_PREC_AUTO threshold on the estimated relative error of p_hat
-    double* part;                 // [nb][n_chunks][10]
+    double* part;                 // [nb][n_chunks][kApproxPartStride]
     unsigned long long* counters; // [0] flips, [1] executed eta x eta LUs, [2] rank-one-form minors, [3] flagged
     ApproxBlockDev blk[kMaxBlocks];
 };

@@ -135,3 +135,35 @@ def test_approx_lucj52_approx_full_trajectory_count_sampled(lib):
     p64, _, st64 = run_approx(lib, c, bits, t, 0, lib.EF_PREC_FP64)
     assert np.max(np.abs(p - p64) / np.maximum(p64, floor)) <= 1e-5
     assert st["sampled_flips"] == st64["sampled_flips"]
+
+
+# Raw Estimate circuits of the 64-circuit uneven batch with few modes and many
+# controlled-phase gates (strong cancellation between trajectories): 34 is
+# n=12, 3+3 particles, k=22; 2 is n=12, k=24; 33 is n=16, k=21.
+BATCH_CANCELLING = [34, 2, 33]
+
+
+@pytest.mark.parametrize("ci", BATCH_CANCELLING)
+def test_approx_auto_on_cancelling_batch_circuits(lib, ci):
+    """EF_PREC_AUTO against the FP64 path on the same trajectories (t =
+    ceil(extent 1e4)), 1500 bitstrings of each circuit, within 1e-5 of
+    max(p, p_floor); FP32 minors alone: the estimate bounds the observed
+    error. Every trajectory that flips a given gate or flippable pair reuses
+    the same rounded ratio and K entry, so these roundings add up over the
+    trajectories instead of averaging out; the kernel corrects them to first
+    order. The oracle checks the FP64 path on one bitstring."""
+    c, bits, mode = W.uneven_batch64()[ci]
+    assert mode == "approx"
+    bits = bits[:1500]
+    t = int(min(math.ceil(O.extent(c.gates) * 1e4), 10 ** 6))
+    p64, _, _ = run_approx(lib, c, bits, t, 7, lib.EF_PREC_FP64)
+    pa, _, st, ea = run_approx(lib, c, bits, t, 7, lib.EF_PREC_AUTO, want_err=True)
+    p32, _, _, e32 = run_approx(lib, c, bits, t, 7, lib.EF_PREC_FP32_MINOR, want_err=True)
+    floor = 1e-6 / math.comb(c.n_modes // 2, len(c.occupied_modes()) // 2) ** 2
+    den = np.maximum(p64, floor)
+    assert np.max(np.abs(pa - p64) / den) <= 1e-5
+    assert np.all(np.abs(p32 - p64) / den <= e32 + 1e-9)
+    assert st["fp64_recomputed"] == np.count_nonzero(ea < 0)
+    j = int(np.argmax(np.abs(p32 - p64) / den))
+    p_ref, _ = O.raw_estimate(c, bits[j:j + 1], t=t, seed=7, b_indices=[j])
+    assert abs(p64[j] - p_ref[0]) <= 1e-10 * max(p_ref[0], floor)
