@@ -54,12 +54,13 @@ METRIC = "Born-rule probabilities/s and branch-dets/s at rel err ≤1e-5 vs FP64
 UNIT = "probabilities/s"
 NB = 10_000
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_exact_lu_f32<8> launch on this workload
-# (ncu, GB300, `-k regex:"k_exact_lu_f32|k_exact_combine_wp" -s 9 -c 6` on `bench.py --steps 3
-# --warmup 3 --no-cpu-baseline --no-fp64-form --no-secondary`): one launch covers both mode blocks;
-# of the 82 MB of FP32 determinants it writes, 24-27 MB reach DRAM within the launch and the rest
-# stays in L2 until the combine; the pattern matrices are read from L2. To be re-measured whenever
-# that kernel changes.
-LU_DRAM_BYTES_PER_LAUNCH = 26_846_848  # mean of two launches (28.4 MB, 25.3 MB), 8-pattern chunks
+# (ncu, GB300, `--metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+# -k regex:"k_exact|k_build"` on `bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-fp64-form
+# --no-secondary`; ncu empties the caches before each launch): one launch covers both mode blocks;
+# of the 51 MB of FP32 results (float2 value + bfloat16 error term per minor) it writes, about
+# 2.3 MB reach DRAM within the launch and the rest stays in L2 until the combine; the pattern
+# matrices and bitstrings are read cold (2.3 MB). To be re-measured whenever that kernel changes.
+LU_DRAM_BYTES_PER_LAUNCH = 4_573_013  # mean of the last three launches (4.57, 4.46, 4.69 MB)
 L2_BYTES = 129 * 2 ** 20
 WORKLOAD = ("LUCJ exact: 2x16 modes (32 qubits), 8a+8b, k=16 controlled-phase gates "
             "(4 aa + 4 bb neighbour, 8 ab on-site, N(0,0.1)), 2^16 branches, 10^4 sector bitstrings")

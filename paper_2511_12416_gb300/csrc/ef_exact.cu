@@ -1070,15 +1070,35 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
             const int B = row < rows0 ? 0 : 1;
             const int z0 = (B ? row - rows0 : row) << RL;
             float4 v[NL];
+            // the row's NL determinants and error terms are contiguous and start at a
+            // multiple of NL: read them as 16-byte (and, below 8 error terms, 4- or
+            // 8-byte) vectors
+            const size_t base = dix(col, (uint32_t)z0, C.r[B]);
+            const float4* dv = reinterpret_cast<const float4*>(C.D32[B] + base);
+            uint32_t ew[(NL + 1) / 2];
+            if constexpr (NL >= 8) {
 #pragma unroll
-            for (int l = 0; l < NL; ++l) {
-                const size_t idx = dix(col, (uint32_t)(z0 | l), C.r[B]);
-                const float2 d = C.D32[B][idx];
-                const uint16_t ec = C.E32[B][idx];
-                errt[rr][l] = want_err ? err_term_value(ec) : 0.f;
-                v[l] = make_float4(d.x, 0.f, d.y, 0.f);
-                if (C.src == 2 && err_redone(ec))  // redone in FP64, stored as a float pair
-                    v[l] = reinterpret_cast<const float4*>(C.D64[B])[idx];
+                for (int q = 0; q < NL / 8; ++q) {
+                    const uint4 w = reinterpret_cast<const uint4*>(C.E32[B] + base)[q];
+                    ew[4 * q] = w.x, ew[4 * q + 1] = w.y, ew[4 * q + 2] = w.z, ew[4 * q + 3] = w.w;
+                }
+            } else if constexpr (NL == 4) {
+                const uint2 w = *reinterpret_cast<const uint2*>(C.E32[B] + base);
+                ew[0] = w.x, ew[1] = w.y;
+            } else {
+                ew[0] = *reinterpret_cast<const uint32_t*>(C.E32[B] + base);
+            }
+#pragma unroll
+            for (int l = 0; l < NL; l += 2) {
+                const float4 dd = dv[l / 2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint16_t ec = (uint16_t)(ew[l / 2] >> (16 * h));
+                    errt[rr][l + h] = want_err ? err_term_value(ec) : 0.f;
+                    v[l + h] = h ? make_float4(dd.z, 0.f, dd.w, 0.f) : make_float4(dd.x, 0.f, dd.y, 0.f);
+                    if (C.src == 2 && err_redone(ec))  // redone in FP64, stored as a float pair
+                        v[l + h] = reinterpret_cast<const float4*>(C.D64[B])[base + l + h];
+                }
             }
             row_wht<RL>(v, cf_add, cf_sub);
             const float4* Wh = C.OmegaHatDF[B];

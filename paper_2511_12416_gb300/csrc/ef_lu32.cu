@@ -49,6 +49,10 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B0, ExactBlo
         }
         __syncthreads();
         if (b >= nb) continue;
+        // error terms of four consecutive patterns go out as one 8-byte store
+        // (chunks of at least 4 patterns start at a multiple of 4)
+        const bool pack = Y >= 4;
+        uint64_t codes = 0;
         for (int t = 0; t < Y; ++t) {
             const size_t z = (size_t)chunk * Y + t;
             float2 det = make_float2(0.f, 0.f);
@@ -68,7 +72,12 @@ __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B0, ExactBlo
             }
             const size_t o = dix(b, (uint32_t)z, B.r);
             B.D32[o] = det;
-            B.E32[o] = ec;
+            if (!pack) {
+                B.E32[o] = ec;
+            } else {
+                codes = (codes >> 16) | ((uint64_t)ec << 48);
+                if ((t & 3) == 3) *reinterpret_cast<uint64_t*>(B.E32 + o - 3) = codes;
+            }
         }
     }
 }
@@ -156,6 +165,8 @@ __global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restri
         if (b < E.nb) {
             int rows[ETA];
             const bool ok = decode_rows<ETA>(E.bits[2 * b], E.bits[2 * b + 1], B.mask0, B.mask1, rows);
+            const bool pack = Y >= 4;  // as in k_exact_lu_f32
+            uint64_t codes = 0;
             for (int t = 0; t < Y; ++t) {
                 const size_t z = (size_t)chunk * Y + t;
                 float2 det = make_float2(0.f, 0.f);
@@ -175,7 +186,12 @@ __global__ void __launch_bounds__(128) k_queue_lu_f32(const QueueEntry* __restri
                 }
                 const size_t o = dix(b, (uint32_t)z, B.r);
                 B.D32[o] = det;
-                B.E32[o] = ec;
+                if (!pack) {
+                    B.E32[o] = ec;
+                } else {
+                    codes = (codes >> 16) | ((uint64_t)ec << 48);
+                    if ((t & 3) == 3) *reinterpret_cast<uint64_t*>(B.E32 + o - 3) = codes;
+                }
             }
         }
         __syncthreads();
