@@ -85,10 +85,12 @@ typedef enum {
     EF_PREC_FP32_MINOR = 1, /* minors and LU in FP32, branch sum in FP64 */
     EF_PREC_AUTO = 2        /* FP32 minors; Exact: for results whose error estimate
                                exceeds tol the determinants carrying most of the
-                               estimated error are redone in FP64, then the result
-                               is re-estimated and, if still above tol, all of its
-                               determinants are redone in FP64; Raw Estimate: such
-                               results are recomputed in FP64 */
+                               estimated error are redone in float-pair arithmetic
+                               (about 48 bits, on the FP32 pipes; at most 8 particles
+                               per block), then the result is re-estimated and, if
+                               still above tol, all of its determinants are redone
+                               in FP64; Raw Estimate: such results are recomputed
+                               in FP64 */
 } ef_precision;
 
 enum {
@@ -107,9 +109,9 @@ typedef struct {
     int64_t logical_branch_dets;  /* (bitstring, branch or trajectory) pairs the call evaluated */
     int64_t executed_minor_lus;   /* LU factorizations of minors actually run */
     int64_t fp64_recomputed;      /* EF_PREC_AUTO: flagged bitstrings, whose largest-error determinants
-                                     (or, if still above tol, all of them) were redone in FP64 (Exact),
-                                     or which were recomputed in FP64 (Raw Estimate); the FP64
-                                     determinants are counted in executed_minor_lus */
+                                     were redone in float pairs (or, if still above tol, all of them in
+                                     FP64) (Exact), or which were recomputed in FP64 (Raw Estimate); the
+                                     redone determinants are counted in executed_minor_lus */
     int64_t kernel_launches;      /* kernels this library launched in the call */
     int64_t sampled_flips;        /* Raw Estimate: number of x_j = 1 over all trajectories */
     double max_est_rel_err;       /* largest per-result error estimate of the FP32 path */
@@ -156,7 +158,7 @@ int ef_circuit_set_precision(ef_circuit* c, int32_t precision, double tol);
 /* Exact algorithm (Eqs. 8-9) for bitstrings bits[0..nb) (host, nb x 2 uint64).
  * out[nb]: probabilities. err_out[nb] (nullable): per-result estimate of the
  * relative error of the FP32-minor path (0 on the FP64 path; for results
- * redone in FP64 under EF_PREC_AUTO, the FP32 estimate that triggered it,
+ * redone under EF_PREC_AUTO, the FP32 estimate that triggered it,
  * negated). nb = 0 is allowed. The circuit's 2^k trajectories are enumerated
  * per independent mode block as distinct flip patterns; controlled-phase
  * gates whose modes no Givens rotation touches before them, or after them,

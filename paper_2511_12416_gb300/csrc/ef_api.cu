@@ -1070,12 +1070,12 @@ int exact_enqueue_combine(ef_circuit* c, const ExactBuffers& eb, ef::ExactCombin
     cm.recomp = eb.recomp;
     if (per_minor) {
         if (c->nblocks == 2 && eb.blk[0].eta == eb.blk[1].eta) {
-            EF_CK(ef::launch_exact_lu_f64_minors(eb.blk[0], eb.blk[1], 2, bits, eb.mlist[0], eb.mlist[1], eb.count + 2,
-                                                 nbb, s, st));
+            EF_CK(ef::launch_exact_lu_redo_minors(eb.blk[0], eb.blk[1], 2, bits, eb.mlist[0], eb.mlist[1],
+                                                  eb.count + 2, s, st));
         } else {
             for (int b = 0; b < c->nblocks; ++b)
-                EF_CK(ef::launch_exact_lu_f64_minors(eb.blk[b], eb.blk[b], 1, bits, eb.mlist[b], nullptr,
-                                                     eb.count + 2 + b, nbb, s, st));
+                EF_CK(ef::launch_exact_lu_redo_minors(eb.blk[b], eb.blk[b], 1, bits, eb.mlist[b], nullptr,
+                                                      eb.count + 2 + b, s, st));
         }
         ef::ExactCombineDev chk = cm;
         chk.src = 2;

@@ -160,73 +160,6 @@ __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const ui
     }
 }
 
-// Thread <-> one listed determinant (bitstring column, pattern z): redone in
-// FP64, stored in its D64 slot as a float pair (re hi, re lo, im hi, im lo),
-// and marked in E32 (kErrRedone). One launch covers the lists of nblk blocks of
-// the same particle count (items of block 1 follow those of block 0): the
-// run time is set by one warp's serial FP64 instruction stream, so a second
-// launch would double it.
-template <int ETA>
-__global__ void __launch_bounds__(128) k_exact_lu_f64m(ExactBlockDev B0, ExactBlockDev B1, int nblk,
-                                                       const uint64_t* __restrict__ bits,
-                                                       const int2* __restrict__ mlist0,
-                                                       const int2* __restrict__ mlist1,
-                                                       const int* __restrict__ mcount, int64_t stride) {
-    const int64_t c0 = mcount[0];
-    const int64_t count = c0 + (nblk > 1 ? (int64_t)mcount[1] : 0);
-    for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < count;
-         item += (int64_t)gridDim.x * blockDim.x) {
-        const bool second = item >= c0;
-        const ExactBlockDev& B = second ? B1 : B0;
-        const int2 e = second ? mlist1[item - c0] : mlist0[item];
-        const int64_t pos = e.x;
-        const int z = e.y;
-        int rows[ETA];
-        double2 res = make_double2(0.0, 0.0);
-        if (decode_rows<ETA>(bits[2 * pos], bits[2 * pos + 1], B.mask0, B.mask1, rows)) {
-            const double2* Mz = B.M64 + (size_t)z * B.n * ETA;
-            double2 A[ETA][ETA];
-#pragma unroll
-            for (int i = 0; i < ETA; ++i)
-#pragma unroll
-                for (int j = 0; j < ETA; ++j) A[i][j] = Mz[rows[i] * ETA + j];
-            res = lu_det_plain<double, ETA>(A);
-        }
-        const float xh = (float)res.x, yh = (float)res.y;
-        reinterpret_cast<float4*>(B.D64)[dix(pos, (uint32_t)z, B.r)] =
-            make_float4(xh, (float)(res.x - (double)xh), yh, (float)(res.y - (double)yh));
-        B.E32[dix(pos, (uint32_t)z, B.r)] = kErrRedone;
-    }
-}
-
-template <int ETA>
-static cudaError_t launch_f64m_eta(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, const uint64_t* bits,
-                                   const int2* mlist0, const int2* mlist1, const int* mcount, int64_t stride,
-                                   cudaStream_t s) {
-    k_exact_lu_f64m<ETA><<<sm_count() * 8, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_exact_lu_f64_minors(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk,
-                                       const uint64_t* bits, const int2* mlist0, const int2* mlist1,
-                                       const int* mcount, int64_t stride, cudaStream_t s, LaunchStats& st) {
-    if (nblk > 1 && b1.eta != b0.eta) return cudaErrorInvalidValue;
-    cudaError_t e;
-    switch (b0.eta) {
-        case 1: e = launch_f64m_eta<1>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
-        case 2: e = launch_f64m_eta<2>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
-        case 3: e = launch_f64m_eta<3>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
-        case 4: e = launch_f64m_eta<4>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
-        case 5: e = launch_f64m_eta<5>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
-        case 6: e = launch_f64m_eta<6>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
-        case 7: e = launch_f64m_eta<7>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
-        case 8: e = launch_f64m_eta<8>(b0, b1, nblk, bits, mlist0, mlist1, mcount, stride, s); break;
-        default: return cudaErrorInvalidValue;
-    }
-    st.launches += 1;
-    return e;
-}
-
 template <int ETA>
 static cudaError_t launch_f64t_eta(const ExactBlockDev& b, const uint64_t* bits, int64_t nb, const int* list,
                                    const int* list_count, int64_t stride, cudaStream_t s) {
@@ -406,6 +339,139 @@ __device__ __forceinline__ float4 cf_mul(float4 a, float4 b) {
     const float2 r = ff_add(ff_mul(ar, br), ff_neg(ff_mul(ai, bi)));
     const float2 i = ff_add(ff_mul(ar, bi), ff_mul(ai, br));
     return make_float4(r.x, r.y, i.x, i.y);
+}
+
+// ---- float-pair LU for the listed determinants of EF_PREC_AUTO (the FP32
+// results whose error estimate called for a recompute). On this GPU an FP64
+// instruction costs a warp about 64 cycles of its sub-partition's FP64 unit
+// whatever its active lanes, so the thread-per-determinant FP64 LU ran as
+// long as one warp's serial FP64 stream (about 40 us for the 32-qubit
+// workload's 10^4 listed determinants). Float pairs (about 48 bits) run on
+// the FP32 pipes. The result is stored as a float pair, as the FP64 one was.
+
+__device__ __forceinline__ float2 ff_sub(float2 x, float2 y) { return ff_add(x, ff_neg(y)); }
+// 1 / x for x > 0: the FP32 reciprocal refined by one Newton step in float
+// pairs, r = r0 + r0 (1 - x r0) (as in Bailey's double-double division)
+__device__ __forceinline__ float2 ff_recip(float2 x) {
+    const float r0 = 1.0f / x.x;
+    const float2 e = ff_sub(make_float2(1.f, 0.f), ff_mul(x, make_float2(r0, 0.f)));
+    return ff_add(make_float2(r0, 0.f), ff_mul(make_float2(r0, 0.f), e));
+}
+__device__ __forceinline__ float4 cf_shfl(float4 v, int src, int width) {
+    const unsigned full = 0xffffffffu;
+    return make_float4(__shfl_sync(full, v.x, src, width), __shfl_sync(full, v.y, src, width),
+                       __shfl_sync(full, v.z, src, width), __shfl_sync(full, v.w, src, width));
+}
+__device__ __forceinline__ float4 cf_from_d(double2 a) {
+    const float rh = (float)a.x, ih = (float)a.y;
+    return make_float4(rh, (float)(a.x - (double)rh), ih, (float)(a.y - (double)ih));
+}
+
+// A group of G lanes (G a power of two, eta <= G <= 32) factors one listed
+// minor; lane r holds row r (float pairs) and the rows never move: at step k
+// the group picks the pivot row p (largest |a_rk|^2 of the leading parts
+// among rows not yet used, lowest r on ties), broadcasts its entries, and the
+// other unused rows eliminate against it. The sign of the permutation is the
+// parity of the unused rows below p at each step.
+template <int G>
+__global__ void __launch_bounds__(128) k_exact_lu_ffm(ExactBlockDev B0, ExactBlockDev B1, int nblk,
+                                                      const uint64_t* __restrict__ bits,
+                                                      const int2* __restrict__ mlist0,
+                                                      const int2* __restrict__ mlist1,
+                                                      const int* __restrict__ mcount) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int r = lane & (G - 1);
+    const int gbase = lane & ~(G - 1);
+    const unsigned gmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    constexpr int GPW = 32 / G;
+    const int64_t c0 = mcount[0];
+    const int64_t count = c0 + (nblk > 1 ? (int64_t)mcount[1] : 0);
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wbase = warp_global * GPW; wbase < count; wbase += nwarps * GPW) {
+        const int64_t item = wbase + lane / G;
+        const bool valid = item < count;
+        const bool second = valid && item >= c0;
+        const ExactBlockDev& B = second ? B1 : B0;
+        const int eta = B.eta;
+        int64_t pos = 0;
+        int z = 0, row_idx = -1, cnt = -1;
+        if (valid) {
+            const int2 e = second ? mlist1[item - c0] : mlist0[item];
+            pos = e.x;
+            z = e.y;
+            row_idx = nth_row(bits[2 * pos], bits[2 * pos + 1], B.mask0, B.mask1, r, cnt);
+        }
+        const bool ok = valid && cnt == eta;
+        float4 row[G];
+        const double2* src = B.M64 + ((size_t)z * B.n + (size_t)(row_idx < 0 ? 0 : row_idx)) * eta;
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            row[j] = (ok && r < eta && j < eta) ? cf_from_d(src[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        bool done = !ok || r >= eta;
+        float4 d = make_float4(1.f, 0.f, 0.f, 0.f);
+        int inv = 0;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            if (k >= eta) break;  // eta is the same in every lane of a warp (both blocks share it)
+            float mag = done ? -1.f : fmaf(row[k].x, row[k].x, row[k].z * row[k].z);
+            int idx = r;
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                const float om = __shfl_xor_sync(full, mag, off, G);
+                const int oi = __shfl_xor_sync(full, idx, off, G);
+                if (om > mag || (om == mag && oi < idx)) {
+                    mag = om;
+                    idx = oi;
+                }
+            }
+            const int p = idx;
+            const unsigned act = (__ballot_sync(full, !done) >> gbase) & gmask;
+            inv += __popc(act & ((1u << p) - 1u));
+            const float4 piv = cf_shfl(row[k], p, G);
+            d = cf_mul(d, piv);
+            // 1 / pivot = conj(pivot) / |pivot|^2; a vanishing pivot leaves det 0 and
+            // the rows unchanged
+            const float2 pr = make_float2(piv.x, piv.y), pi = make_float2(piv.z, piv.w);
+            const float2 n2 = ff_add(ff_mul(pr, pr), ff_mul(pi, pi));
+            const bool nz = n2.x >= 1.17549435e-38f;
+            const float2 rn = nz ? ff_recip(n2) : make_float2(0.f, 0.f);
+            const float2 ipr = ff_mul(pr, rn), ipi = ff_neg(ff_mul(pi, rn));
+            const bool upd = !done && r != p;
+            const float4 l = cf_mul(row[k], make_float4(ipr.x, ipr.y, ipi.x, ipi.y));
+#pragma unroll
+            for (int j = k + 1; j < G; ++j) {
+                if (j >= eta) break;
+                const float4 pj = cf_shfl(row[j], p, G);
+                if (upd) row[j] = cf_sub(row[j], cf_mul(l, pj));
+            }
+            if (r == p) done = true;
+        }
+        if (valid && r == 0) {
+            const float4 det = !ok ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                   : ((inv & 1) ? make_float4(-d.x, -d.y, -d.z, -d.w) : d);
+            const size_t o = dix(pos, (uint32_t)z, B.r);
+            reinterpret_cast<float4*>(B.D64)[o] = det;
+            B.E32[o] = kErrRedone;
+        }
+    }
+}
+
+cudaError_t launch_exact_lu_redo_minors(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk,
+                                        const uint64_t* bits, const int2* mlist0, const int2* mlist1,
+                                        const int* mcount, cudaStream_t s, LaunchStats& st) {
+    if (nblk > 1 && b1.eta != b0.eta) return cudaErrorInvalidValue;
+    if (b0.eta < 1 || b0.eta > 16) return cudaErrorInvalidValue;
+    st.launches += 1;
+    // the count lives on the device: a fixed grid of one wave strides over the list
+    const int grid = sm_count() * 4;
+    const int eta = b0.eta;
+    if (eta <= 2) k_exact_lu_ffm<2><<<grid, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    else if (eta <= 4) k_exact_lu_ffm<4><<<grid, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    else if (eta <= 8) k_exact_lu_ffm<8><<<grid, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    else k_exact_lu_ffm<16><<<grid, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    return cudaGetLastError();
 }
 
 // Walsh-Hadamard stage over bit j on float pairs, optionally followed by the

@@ -201,11 +201,11 @@ cudaError_t launch_queue_lu_f32(int eta, const QueueEntry* entries, int n_entrie
 cudaError_t launch_exact_lu_f64(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
                                 const int* list, const int* list_count, int64_t cap,
                                 cudaStream_t s, LaunchStats& st);
-// FP64 redo of the listed determinants mlist_B[0..mcount[B]) of nblk blocks
-// with the same eta (<= 8), in one launch
-cudaError_t launch_exact_lu_f64_minors(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk,
-                                       const uint64_t* bits, const int2* mlist0, const int2* mlist1,
-                                       const int* mcount, int64_t stride, cudaStream_t s, LaunchStats& st);
+// Float-pair (about 48-bit) redo of the listed determinants
+// mlist_B[0..mcount[B]) of nblk blocks with the same eta (<= 16), in one launch
+cudaError_t launch_exact_lu_redo_minors(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk,
+                                        const uint64_t* bits, const int2* mlist0, const int2* mlist1,
+                                        const int* mcount, cudaStream_t s, LaunchStats& st);
 cudaError_t launch_exact_lu_rows(const ExactBlockDev& b, const uint64_t* bits, int64_t nb,
                                  const int* list, const int* list_count, int64_t cap,
                                  bool fp64, cudaStream_t s, LaunchStats& st);
