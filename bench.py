@@ -60,7 +60,7 @@ NB = 10_000
 # of the 51 MB of FP32 results (float2 value + bfloat16 error term per minor) it writes, about
 # 2.3 MB reach DRAM within the launch and the rest stays in L2 until the combine; the pattern
 # matrices and bitstrings are read cold (2.3 MB). To be re-measured whenever that kernel changes.
-LU_DRAM_BYTES_PER_LAUNCH = 4_573_013  # mean of the last three launches (4.57, 4.46, 4.69 MB)
+LU_DRAM_BYTES_PER_LAUNCH = 4_580_523  # mean of the last three launches (4.52, 4.72, 4.50 MB)
 L2_BYTES = 129 * 2 ** 20
 WORKLOAD = ("LUCJ exact: 2x16 modes (32 qubits), 8a+8b, k=16 controlled-phase gates "
             "(4 aa + 4 bb neighbour, 8 ab on-site, N(0,0.1)), 2^16 branches, 10^4 sector bitstrings")
