@@ -202,3 +202,23 @@ def test_exact_leaves_probability_neutral_gates_out(lib):
     assert np.max(rel_err(p, O.exact_probabilities(c, bits), 1e-6 / sector_size(c))) <= 1e-10
     assert st["executed_minor_lus"] == 2 * len(bits)
     assert st["logical_branch_dets"] == len(bits) * 2 ** 4
+
+
+def test_exact_auto_tight_tolerance_float_pair_redo(lib):
+    """EF_PREC_AUTO at tol = 1e-9 on 2000 bitstrings of the 32-qubit LUCJ
+    workload: most results need the redo, so many determinants go through the
+    float-pair warp-row LU (about 48 bits) and some results through the
+    whole-bitstring FP64 redo; every result must stay within 1e-9 of the FP64
+    path (pinned to the oracle by the tests above)."""
+    c, bits = W.lucj32_exact(2000)
+    floor = 1e-6 / sector_size(c)
+    p64, _ = run_exact(lib, c, bits, lib.EF_PREC_FP64)
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_AUTO, tol=1e-9)
+    try:
+        p, err = lib.ef_prob_exact(h, bits, want_err=True)
+        st = lib.ef_circuit_get_stats(h)
+    finally:
+        lib.ef_circuit_destroy(h)
+    assert np.max(rel_err(p, p64, floor)) <= 1e-9
+    assert st["fp64_recomputed"] > len(bits) // 2
+    assert st["fp64_recomputed"] == np.count_nonzero(err < 0)
