@@ -66,7 +66,7 @@ __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~(
 
 // Dynamic shared memory of one CTA, identical on host and device.
 struct ApproxSmem {
-    size_t sT, sGp, sA0[kMaxBlocks], sLeft[kMaxBlocks], sK[kMaxBlocks], aug, lam, yrow, total;
+    size_t sT, sQr, sGp, sA0[kMaxBlocks], sLeft[kMaxBlocks], sK[kMaxBlocks], aug, lam, yrow, total;
 };
 
 __host__ __device__ inline ApproxSmem approx_smem(const ApproxDev& A, int eta_t, size_t csz) {
@@ -74,6 +74,8 @@ __host__ __device__ inline ApproxSmem approx_smem(const ApproxDev& A, int eta_t,
     size_t off = 0;
     const int k16 = (A.k + 15) & ~15;
     s.sT = off;
+    off = al16(off + (size_t)k16 * 4);
+    s.sQr = off;  // FP32 ratios (FP32 path)
     off = al16(off + (size_t)k16 * 4);
     s.sGp = off;
     if (A.kform) off = al16(off + (size_t)A.nblocks * A.k * 8);
@@ -488,11 +490,15 @@ __global__ void __launch_bounds__(kApproxThreads, approx_min_ctas<R, ETA>())
     const ApproxSmem L = approx_smem(A, ETA, sizeof(T));
     uint32_t* sT = reinterpret_cast<uint32_t*>(sm_raw + L.sT);
     uint64_t* sGp = reinterpret_cast<uint64_t*>(sm_raw + L.sGp);
+    float* sQr = reinterpret_cast<float*>(sm_raw + L.sQr);
     double2* aug = reinterpret_cast<double2*>(sm_raw + L.aug);  // [ETA][2 ETA]
     double2* lam = reinterpret_cast<double2*>(sm_raw + L.lam);  // [L][ETA][n] FP64 Lambda_l rows
     double2* yrow = reinterpret_cast<double2*>(sm_raw + L.yrow);  // [f][ETA] (rho_a A0^{-1}) rows
     const int k16 = (k + 15) & ~15;
-    for (int j = tid; j < k16; j += NT) sT[j] = (j < k) ? A.T[j] : 0u;
+    for (int j = tid; j < k16; j += NT) {
+        sT[j] = (j < k) ? A.T[j] : 0u;
+        if constexpr (kF32) sQr[j] = (j < k) ? A.qratio32[j] : 0.f;
+    }
     if (A.kform)
         for (int e = tid; e < A.nblocks * k; e += NT) sGp[e] = A.gpair[e];
 
@@ -746,8 +752,14 @@ __global__ void __launch_bounds__(kApproxThreads, approx_min_ctas<R, ETA>())
                 // gate j flipped: its ratio and its flips (layer, modes; pairs for the K form)
                 auto flip = [&](int j) {
                     ++nflip;
-                    if constexpr (kF32) rq *= A.qratio32[j];
+                    if constexpr (kF32) rq *= sQr[j];
                     else rq *= A.qratio[j];
+                    if (A.kform) {  // the pair masks alone (zero for a block the gate does not touch)
+#pragma unroll
+                        for (int B = 0; B < kMaxBlocks; ++B)
+                            if (B < A.nblocks) Nm[B] ^= sGp[B * k + j];
+                        return;
+                    }
 #pragma unroll
                     for (int B = 0; B < kMaxBlocks; ++B) {
                         if (B >= A.nblocks) break;
