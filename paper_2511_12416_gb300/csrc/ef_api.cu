@@ -94,12 +94,12 @@ cudaError_t upload(DBuf& d, const std::vector<T>& h, cudaStream_t s) {
     return cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
 }
 
-// complex values as float pairs (re hi, re lo, im hi, im lo), hi + lo = value to ~48 bits
+// complex values as float pairs (re hi, im hi, re lo, im lo), hi + lo = value to ~48 bits
 std::vector<float4> to_ff(const std::vector<cd>& v) {
     std::vector<float4> o(v.size());
     for (size_t i = 0; i < v.size(); ++i) {
         const float rh = (float)v[i].real(), ih = (float)v[i].imag();
-        o[i] = make_float4(rh, (float)(v[i].real() - (double)rh), ih, (float)(v[i].imag() - (double)ih));
+        o[i] = make_float4(rh, ih, (float)(v[i].real() - (double)rh), (float)(v[i].imag() - (double)ih));
     }
     return o;
 }

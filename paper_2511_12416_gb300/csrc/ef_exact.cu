@@ -322,23 +322,62 @@ __device__ __forceinline__ float2 ff_mul(float2 x, float2 y) {
     const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));
     return quick_two_sum(p, e);
 }
-// complex float pairs as float4 (re hi, re lo, im hi, im lo)
+// Complex float pairs as float4 (re hi, im hi, re lo, im lo): the leading
+// parts form one FP32 complex and the trailing parts another, so the real and
+// imaginary float-pair operations run as packed FP32x2 instructions, one
+// instruction for both (each component is rounded exactly as the scalar
+// operation would be).
+__device__ __forceinline__ float2 cf_re(float4 v) { return make_float2(v.x, v.z); }
+__device__ __forceinline__ float2 cf_im(float4 v) { return make_float2(v.y, v.w); }
+__device__ __forceinline__ float2 cf_hi(float4 v) { return make_float2(v.x, v.y); }  // leading parts (FP32 complex)
+__device__ __forceinline__ float4 cf_make(float2 re, float2 im) { return make_float4(re.x, im.x, re.y, im.y); }
+__device__ __forceinline__ float4 cf_from_f(float2 z) { return make_float4(z.x, z.y, 0.f, 0.f); }
+
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+__device__ __forceinline__ float2 p2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 p2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+#else
+__device__ __forceinline__ float2 p2_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 p2_mul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+#endif
+
+// Two float-pair additions at once: ff_add on (xh.x, xl.x) + (yh.x, yl.x) and
+// on the .y components, in ff_add's order of operations.
 __device__ __forceinline__ float4 cf_add(float4 a, float4 b) {
-    const float2 r = ff_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
-    const float2 i = ff_add(make_float2(a.z, a.w), make_float2(b.z, b.w));
-    return make_float4(r.x, r.y, i.x, i.y);
+    const float2 ah = make_float2(a.x, a.y), al = make_float2(a.z, a.w);
+    const float2 bh = make_float2(b.x, b.y), bl = make_float2(b.z, b.w);
+    const float2 s = p2_add(ah, bh);
+    const float2 bb = p2_sub(s, ah);
+    const float2 e = p2_add(p2_sub(ah, p2_sub(s, bb)), p2_sub(bh, bb));
+    const float2 t = p2_add(e, p2_add(al, bl));
+    const float2 r = p2_add(s, t);
+    const float2 lo = p2_sub(t, p2_sub(r, s));
+    return make_float4(r.x, r.y, lo.x, lo.y);
 }
-__device__ __forceinline__ float4 cf_sub(float4 a, float4 b) {
-    const float2 r = ff_add(make_float2(a.x, a.y), ff_neg(make_float2(b.x, b.y)));
-    const float2 i = ff_add(make_float2(a.z, a.w), ff_neg(make_float2(b.z, b.w)));
-    return make_float4(r.x, r.y, i.x, i.y);
+__device__ __forceinline__ float4 cf_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 cf_sub(float4 a, float4 b) { return cf_add(a, cf_neg(b)); }
+// Two float-pair products at once (ff_mul's order of operations).
+__device__ __forceinline__ float4 cf_mul2(float2 xh, float2 xl, float2 yh, float2 yl) {
+    const float2 p = p2_mul(xh, yh);
+    const float2 e = p2_fma(xh, yl, p2_fma(xl, yh, p2_fma(xh, yh, make_float2(-p.x, -p.y))));
+    const float2 s = p2_add(p, e);
+    const float2 lo = p2_sub(e, p2_sub(s, p));
+    return make_float4(s.x, s.y, lo.x, lo.y);
 }
+// complex product: (ar br, ar bi) + (-ai bi, ai br), as the scalar
+// ff_add(ff_mul(ar, br), -ff_mul(ai, bi)) and ff_add(ff_mul(ar, bi), ff_mul(ai, br))
 __device__ __forceinline__ float4 cf_mul(float4 a, float4 b) {
-    const float2 ar = make_float2(a.x, a.y), ai = make_float2(a.z, a.w);
-    const float2 br = make_float2(b.x, b.y), bi = make_float2(b.z, b.w);
-    const float2 r = ff_add(ff_mul(ar, br), ff_neg(ff_mul(ai, bi)));
-    const float2 i = ff_add(ff_mul(ar, bi), ff_mul(ai, br));
-    return make_float4(r.x, r.y, i.x, i.y);
+    const float4 p1 = cf_mul2(make_float2(a.x, a.x), make_float2(a.z, a.z), make_float2(b.x, b.y),
+                              make_float2(b.z, b.w));
+    const float4 p2 = cf_mul2(make_float2(-a.y, a.y), make_float2(-a.w, a.w), make_float2(b.y, b.x),
+                              make_float2(b.w, b.z));
+    return cf_add(p1, p2);
 }
 
 // ---- float-pair LU for the listed determinants of EF_PREC_AUTO (the FP32
@@ -364,7 +403,7 @@ __device__ __forceinline__ float4 cf_shfl(float4 v, int src, int width) {
 }
 __device__ __forceinline__ float4 cf_from_d(double2 a) {
     const float rh = (float)a.x, ih = (float)a.y;
-    return make_float4(rh, (float)(a.x - (double)rh), ih, (float)(a.y - (double)ih));
+    return make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
 }
 
 // A group of G lanes (G a power of two, eta <= G <= 32) factors one listed
@@ -415,7 +454,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_ffm(ExactBlockDev B0, ExactBlo
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             if (k >= eta) break;  // eta is the same in every lane of a warp (both blocks share it)
-            float mag = done ? -1.f : fmaf(row[k].x, row[k].x, row[k].z * row[k].z);
+            float mag = done ? -1.f : fmaf(row[k].x, row[k].x, row[k].y * row[k].y);
             int idx = r;
 #pragma unroll
             for (int off = G / 2; off > 0; off >>= 1) {
@@ -433,13 +472,13 @@ __global__ void __launch_bounds__(128) k_exact_lu_ffm(ExactBlockDev B0, ExactBlo
             d = cf_mul(d, piv);
             // 1 / pivot = conj(pivot) / |pivot|^2; a vanishing pivot leaves det 0 and
             // the rows unchanged
-            const float2 pr = make_float2(piv.x, piv.y), pi = make_float2(piv.z, piv.w);
+            const float2 pr = cf_re(piv), pi = cf_im(piv);
             const float2 n2 = ff_add(ff_mul(pr, pr), ff_mul(pi, pi));
             const bool nz = n2.x >= 1.17549435e-38f;
             const float2 rn = nz ? ff_recip(n2) : make_float2(0.f, 0.f);
             const float2 ipr = ff_mul(pr, rn), ipi = ff_neg(ff_mul(pi, rn));
             const bool upd = !done && r != p;
-            const float4 l = cf_mul(row[k], make_float4(ipr.x, ipr.y, ipi.x, ipi.y));
+            const float4 l = cf_mul(row[k], cf_make(ipr, ipi));
 #pragma unroll
             for (int j = k + 1; j < G; ++j) {
                 if (j >= eta) break;
@@ -521,12 +560,12 @@ __device__ __forceinline__ double neg_abs_int(double x) {
 
 // Determinant z of block B for D column col, as the combine's source says. A
 // determinant redone in FP64 for a marked FP32 entry is stored as a float
-// pair (re hi, re lo, im hi, im lo) in its D64 slot.
+// pair (re hi, im hi, re lo, im lo) in its D64 slot.
 __device__ __forceinline__ double2 det_at(const ExactCombineDev& C, int B, size_t idx) {
     if (C.src == 1) return C.D64[B][idx];
     if (C.src == 2 && err_redone(C.E32[B][idx])) {
         const float4 f = reinterpret_cast<const float4*>(C.D64[B])[idx];
-        return make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+        return make_double2((double)f.x + (double)f.z, (double)f.y + (double)f.w);
     }
     const float2 v = C.D32[B][idx];
     return make_double2((double)v.x, (double)v.y);
@@ -673,7 +712,7 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
                 const int nz = 1 << C.r[B];
                 for (int z = tid; z < nz; z += NT) {
                     const float2 v = C.D32[B][dix(col, (uint32_t)z, C.r[B])];
-                    GB[z] = make_float4(v.x, 0.f, v.y, 0.f);
+                    GB[z] = cf_from_f(v);
                 }
             }
             __syncthreads();
@@ -691,8 +730,8 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
             for (int xs = tid; xs < nsh; xs += NT) {
                 const float4 a0 = G0[C.s[0][xs]], a1 = G1[C.s[1][xs]];
                 if (want_err) {
-                    smA32[xs] = make_float2(a0.x, a0.z);
-                    smA32[nsh + xs] = make_float2(a1.x, a1.z);
+                    smA32[xs] = cf_hi(a0);
+                    smA32[nsh + xs] = cf_hi(a1);
                 }
                 acc = cf_add(acc, cf_mul(C.WSDF[xs], cf_mul(a0, a1)));
             }
@@ -791,8 +830,8 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
             if (ffw) {
                 acc = redf[0];
                 for (int w = 1; w < NW; ++w) acc = cf_add(acc, redf[w]);
-                ar = (double)acc.x + (double)acc.y;
-                ai = (double)acc.z + (double)acc.w;
+                ar = (double)acc.x + (double)acc.z;
+                ai = (double)acc.y + (double)acc.w;
             } else {
                 ar = red[0];
                 ai = red[NW];
@@ -921,8 +960,8 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
                 const float2 d = C.D32[B][idx];
                 const uint16_t ec = C.E32[B][idx];
                 errt[B][i] = want_err ? err_term_value(ec) : 0.f;
-                float4 v = make_float4(d.x, 0.f, d.y, 0.f);
-                if (C.src == 2 && err_redone(ec))  // redone in FP64, stored as a float pair
+                float4 v = cf_from_f(d);
+                if (C.src == 2 && err_redone(ec))  // redone, stored as a float pair
                     v = reinterpret_cast<const float4*>(C.D64[B])[idx];
                 for (int pass = 0; pass < 2; ++pass)
                     for (int j = 0; j < rl; ++j) {
@@ -937,8 +976,8 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int xs = tid; xs < nsh; xs += NT) {
             const float4 a0 = G0[C.s[0][xs]], a1 = G1[C.s[1][xs]];
-            A32[xs] = make_float2(a0.x, a0.z);
-            A32[nsh + xs] = make_float2(a1.x, a1.z);
+            A32[xs] = cf_hi(a0);
+            A32[nsh + xs] = cf_hi(a1);
             acc = cf_add(acc, cf_mul(C.WSDF[xs], cf_mul(a0, a1)));
         }
         float var = 0.f;
@@ -966,7 +1005,7 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
                             q = lane_butterfly(q, j, (e >> j) & 1);
                             if (pass == 0 && j == rl - 1) {
                                 const float4 w = C.OmegaHatDF[B][e & lm];
-                                q = cmul(q, make_float2(w.x, w.z));
+                                q = cmul(q, cf_hi(w));
                             }
                         }
                     const float vt = fmaf(q.x, q.x, q.y * q.y) * errt[B][i];
@@ -999,8 +1038,7 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
         float budget = -1.f;
         if (lane == 0) {
             // p = |amp|^2 in float pairs; one FP64 addition forms the output
-            const float2 pff = ff_add(ff_mul(make_float2(a.x, a.y), make_float2(a.x, a.y)),
-                                      ff_mul(make_float2(a.z, a.w), make_float2(a.z, a.w)));
+            const float2 pff = ff_add(ff_mul(cf_re(a), cf_re(a)), ff_mul(cf_im(a), cf_im(a)));
             out[b] = f2d_int(pff.x) + f2d_int(pff.y);
             // error estimate in FP32: |p~ - p| <= 2 |amp| s + s^2 for an amplitude error s
             const float pf = pff.x, tol = tol_f, ec = ec_f;
@@ -1161,8 +1199,8 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
                 for (int h = 0; h < 2; ++h) {
                     const uint16_t ec = (uint16_t)(ew[l / 2] >> (16 * h));
                     errt[rr][l + h] = want_err ? err_term_value(ec) : 0.f;
-                    v[l + h] = h ? make_float4(dd.z, 0.f, dd.w, 0.f) : make_float4(dd.x, 0.f, dd.y, 0.f);
-                    if (C.src == 2 && err_redone(ec))  // redone in FP64, stored as a float pair
+                    v[l + h] = h ? make_float4(dd.z, dd.w, 0.f, 0.f) : make_float4(dd.x, dd.y, 0.f, 0.f);
+                    if (C.src == 2 && err_redone(ec))  // redone, stored as a float pair
                         v[l + h] = reinterpret_cast<const float4*>(C.D64[B])[base + l + h];
                 }
             }
@@ -1190,12 +1228,12 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
             const float4 a0 = G[p0], a1 = G[p1];
             const float4 w = C.WSDF[xs];
             if (scatter) {
-                const float2 w32 = make_float2(w.x, w.z);
-                Q[p0] = cmul(w32, make_float2(a1.x, a1.z));
-                Q[p1] = cmul(w32, make_float2(a0.x, a0.z));
+                const float2 w32 = cf_hi(w);
+                Q[p0] = cmul(w32, cf_hi(a1));
+                Q[p1] = cmul(w32, cf_hi(a0));
             } else if (want_err) {
-                A32[xs] = make_float2(a0.x, a0.z);
-                A32[nsh + xs] = make_float2(a1.x, a1.z);
+                A32[xs] = cf_hi(a0);
+                A32[nsh + xs] = cf_hi(a1);
             }
             acc = cf_add(acc, cf_mul(w, cf_mul(a0, a1)));
         }
@@ -1233,7 +1271,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
                 row_wht<RL>(q, fadd, fsub);
                 const float4* Wh = C.OmegaHatDF[B];
 #pragma unroll
-                for (int l = 0; l < NL; ++l) q[l] = cmul(q[l], make_float2(Wh[l].x, Wh[l].z));
+                for (int l = 0; l < NL; ++l) q[l] = cmul(q[l], cf_hi(Wh[l]));
                 row_wht<RL>(q, fadd, fsub);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
@@ -1249,8 +1287,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
         float budget = -1.f;
         if (lane == 0) {
             // p = |amp|^2 in float pairs; one FP64 addition forms the output
-            const float2 pff = ff_add(ff_mul(make_float2(acc.x, acc.y), make_float2(acc.x, acc.y)),
-                                      ff_mul(make_float2(acc.z, acc.w), make_float2(acc.z, acc.w)));
+            const float2 pff = ff_add(ff_mul(cf_re(acc), cf_re(acc)), ff_mul(cf_im(acc), cf_im(acc)));
             out[b] = f2d_int(pff.x) + f2d_int(pff.y);
             // |p~ - p| <= 2 |amp| s + s^2 for an amplitude error s (in FP32)
             const float pf = pff.x, tol = tol_f, ec = ec_f;

@@ -74,7 +74,7 @@ struct ExactCombineDev {
     const double2* WS;                 // 2^k_sh weights of the shared gates
     const float2* Omega32[kMaxBlocks]; // FP32 copies for the error estimate
     const double2* OmegaHat[kMaxBlocks];  // 2^r_loc: Walsh-Hadamard transform of Omega times 2^-r_loc
-    const float4* OmegaHatDF[kMaxBlocks]; // the same as float pairs (re hi, re lo, im hi, im lo)
+    const float4* OmegaHatDF[kMaxBlocks]; // the same as float pairs (re hi, im hi, re lo, im lo)
     const float4* WSDF;                   // WS as float pairs
     int wht;                           // 1: XOR convolutions by transforms in shared memory
     int wreg;                          // 1: transforms over FP32 determinants in registers
