@@ -28,6 +28,16 @@ template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
     r.y = fma(a.x, b.y, a.y * b.x);
     return r;
 }
+// FP32 cmul as packed FP32x2 instructions (each component rounded exactly as
+// cmul's); for kernels with registers to spare (the pairs take a few moves)
+__device__ __forceinline__ float2 pcmul(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    const float2 t = __fmul2_rn(make_float2(a.y, a.y), make_float2(b.y, b.x));
+    return __ffma2_rn(make_float2(a.x, a.x), b, make_float2(-t.x, t.y));
+#else
+    return cmul(a, b);
+#endif
+}
 // a - l * p
 template <typename T> __device__ __forceinline__ T cfms(T a, T l, T p) {
     T r;

@@ -1005,7 +1005,7 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
                             q = lane_butterfly(q, j, (e >> j) & 1);
                             if (pass == 0 && j == rl - 1) {
                                 const float4 w = C.OmegaHatDF[B][e & lm];
-                                q = cmul(q, cf_hi(w));
+                                q = pcmul(q, cf_hi(w));
                             }
                         }
                     const float vt = fmaf(q.x, q.x, q.y * q.y) * errt[B][i];
@@ -1229,8 +1229,8 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
             const float4 w = C.WSDF[xs];
             if (scatter) {
                 const float2 w32 = cf_hi(w);
-                Q[p0] = cmul(w32, cf_hi(a1));
-                Q[p1] = cmul(w32, cf_hi(a0));
+                Q[p0] = pcmul(w32, cf_hi(a1));
+                Q[p1] = pcmul(w32, cf_hi(a0));
             } else if (want_err) {
                 A32[xs] = cf_hi(a0);
                 A32[nsh + xs] = cf_hi(a1);
@@ -1261,17 +1261,15 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
                     }
                     for (uint32_t g = C.inv_off[B][z0 | l]; g < C.inv_off[B][(z0 | l) + 1]; ++g) {
                         const uint32_t xs = C.inv_xs[B][g];
-                        const float2 t = cmul(C.WS32[xs], Aoth[xs]);
-                        q[l].x += t.x;
-                        q[l].y += t.y;
+                        q[l] = p2_add(q[l], pcmul(C.WS32[xs], Aoth[xs]));
                     }
                 }
-                const auto fadd = [](float2 a, float2 c) { return make_float2(a.x + c.x, a.y + c.y); };
-                const auto fsub = [](float2 a, float2 c) { return make_float2(a.x - c.x, a.y - c.y); };
+                const auto fadd = [](float2 a, float2 c) { return p2_add(a, c); };
+                const auto fsub = [](float2 a, float2 c) { return p2_sub(a, c); };
                 row_wht<RL>(q, fadd, fsub);
                 const float4* Wh = C.OmegaHatDF[B];
 #pragma unroll
-                for (int l = 0; l < NL; ++l) q[l] = cmul(q[l], cf_hi(Wh[l]));
+                for (int l = 0; l < NL; ++l) q[l] = pcmul(q[l], cf_hi(Wh[l]));
                 row_wht<RL>(q, fadd, fsub);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
