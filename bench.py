@@ -7,8 +7,9 @@ Jastrow layer of k=16 controlled-phase gates (4 aa + 4 bb nearest neighbour,
 8 ab on-site, angles N(0, 0.1)) between a Haar orbital rotation and its
 inverse; 2^16 branches; 10^4 bitstrings uniform in the (8,8) sector). One step
 = one ef_prob_exact_dev call on device-resident bitstrings: branch matrices,
-FP32 minor LUs, float-pair branch sums, per-result error estimate and the FP64
-recomputation of flagged results (EF_PREC_AUTO, tol 1e-5).
+FP32 minor LUs, float-pair branch sums, per-result error estimate and the
+recomputation of flagged results (float pairs, then FP64 for whole bitstrings
+still above tol; EF_PREC_AUTO, tol 1e-5).
 
 The same line carries one sub-object per other workload, each with its device
 time, its dominant kernel against a measured peak and a check against the FP64
@@ -60,7 +61,7 @@ NB = 10_000
 # of the 51 MB of FP32 results (float2 value + bfloat16 error term per minor) it writes, about
 # 2.3 MB reach DRAM within the launch and the rest stays in L2 until the combine; the pattern
 # matrices and bitstrings are read cold (2.3 MB). To be re-measured whenever that kernel changes.
-LU_DRAM_BYTES_PER_LAUNCH = 4_580_523  # mean of the last three launches (4.52, 4.72, 4.50 MB)
+LU_DRAM_BYTES_PER_LAUNCH = 4_600_747  # mean of the last three launches (4.56, 4.61, 4.63 MB)
 L2_BYTES = 129 * 2 ** 20
 WORKLOAD = ("LUCJ exact: 2x16 modes (32 qubits), 8a+8b, k=16 controlled-phase gates "
             "(4 aa + 4 bb neighbour, 8 ab on-site, N(0,0.1)), 2^16 branches, 10^4 sector bitstrings")
@@ -693,8 +694,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "bitstrings_per_gpu": NB, "precision": args.precision,
-                   "arithmetic": "FP32 minors and LU, float-pair (~48-bit) branch sums, FP64 redo of the "
-                                 "determinants that carry a flagged result's estimated error",
+                   "arithmetic": "FP32 minors and LU, float-pair (~48-bit) branch sums, float-pair redo of the "
+                                 "determinants that carry a flagged result's estimated error (FP64 redo of "
+                                 "whole bitstrings still above tol)",
                    "l2": "flushed between timed steps (2x L2 buffer written outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "branch_dets_per_s": branch_dets,
