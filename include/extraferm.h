@@ -241,7 +241,11 @@ int ef_prob_grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const do
  * tables sit at the start of the array: a call copies them in from host
  * memory (ordinary cudaMemcpyAsync from pageable memory) unless the previous
  * call on this device was on the same circuit with the same angles, in which
- * case it finds them in place and copies nothing. Calls whose tables, branch
+ * case it finds them in place and copies nothing. A call that copies cannot
+ * be captured in a CUDA graph (pageable copies are not allowed in a capture);
+ * a call that finds the tables in place, on the stream of the circuit's
+ * previous call, copies, synchronises and allocates nothing and can be
+ * captured and replayed (the tests capture one). Calls whose tables, branch
  * matrices and per-bitstring partials do not fit return EF_EINVAL with the
  * largest batch that fits; split the batch. All calls (on any circuit and
  * any stream) share the array and it keeps the last call's contents, so

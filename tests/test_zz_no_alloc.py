@@ -106,3 +106,38 @@ def test_noalloc_rejects_batches_beyond_the_fixed_scratch(lib):
         assert float(out.abs().max()) == 0.0
     finally:
         lib.ef_circuit_destroy(h)
+
+
+def test_noalloc_call_captured_in_a_cuda_graph(lib):
+    """Once a call has put the circuit's tables in the fixed array, the next
+    call on the same circuit and stream copies nothing, synchronises nothing
+    and allocates nothing, so it can be captured in a CUDA graph; the
+    replayed graph gives the allocating entry point's results."""
+    c, bits = W.lucj32_exact(1500)
+    nb = len(bits)
+    d_bits = torch.from_numpy(np.ascontiguousarray(bits).view(np.int64)).cuda()
+    ref = torch.empty(nb, dtype=torch.float64, device="cuda")
+    out = torch.full((nb,), -1.0, dtype=torch.float64, device="cuda")
+    h_ref = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_AUTO)
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_AUTO)
+    s = torch.cuda.Stream()
+    try:
+        lib.ef_prob_exact_dev(h_ref, d_bits.data_ptr(), nb, ref.data_ptr(), 0, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            lib.ef_prob_exact_noalloc_dev(h, d_bits.data_ptr(), nb, out.data_ptr(), 0, s.cuda_stream)
+        s.synchronize()
+        out.fill_(-1.0)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            lib.ef_prob_exact_noalloc_dev(h, d_bits.data_ptr(), nb, out.data_ptr(), 0, s.cuda_stream)
+        for _ in range(2):
+            g.replay()
+            torch.cuda.synchronize()
+            p, p_ref = out.cpu().numpy(), ref.cpu().numpy()
+            assert np.max(np.abs(p - p_ref) / np.maximum(p_ref, _floor(c))) <= 1e-5
+            out.fill_(-1.0)
+    finally:
+        lib.ef_circuit_destroy(h)
+        lib.ef_circuit_destroy(h_ref)
