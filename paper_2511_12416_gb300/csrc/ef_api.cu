@@ -1144,7 +1144,7 @@ int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
         const size_t ny = (size_t)1 << B.r;
         const size_t ne = (size_t)B.n * B.eta;
         EF_CK(B.dM64.ensure(ny * ne * sizeof(double2)));
-        if (!fp64_only) EF_CK(B.dM32.ensure(ny * ne * sizeof(float2)));
+        if (!fp64_only) EF_CK(B.dM32.ensure(2 * ny * ne * sizeof(float2)));
         const bool d32 = c->opt.precision != EF_PREC_FP64, d64 = c->opt.precision != EF_PREC_FP32_MINOR;
         if (d32) EF_CK(B.dD32.ensure(ny * (size_t)cap * sizeof(float2)));
         if (d32) EF_CK(B.dE32.ensure(ny * (size_t)cap * sizeof(uint16_t)));
@@ -1156,6 +1156,7 @@ int exact_buffers(ef_circuit* c, int64_t cap, ExactBuffers& eb) {
         d.F = B.dF.as<uint32_t>();
         d.M64 = B.dM64.as<double2>();
         d.M32 = fp64_only ? nullptr : B.dM32.as<float2>();
+        d.ML32 = fp64_only ? nullptr : B.dM32.as<float2>() + ny * ne;
         d.D32 = d32 ? B.dD32.as<float2>() : nullptr;
         d.E32 = d32 ? B.dE32.as<uint16_t>() : nullptr;
         d.D64 = d64 ? B.dD64.as<double2>() : nullptr;
@@ -1392,6 +1393,7 @@ int grad_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, const double* d_
         d.F = B.dF.as<uint32_t>();
         d.M64 = B.dM64.as<double2>();
         d.M32 = nullptr;
+        d.ML32 = nullptr;
         d.D32 = nullptr;
         d.E32 = nullptr;
         d.D64 = B.dD64.as<double2>();
@@ -2151,6 +2153,7 @@ size_t noalloc_layout(ef_circuit* c, int64_t nb, bool want32, unsigned char* bas
         ef::ExactBlockDev& d = eb.blk[b];
         d.M64 = cv.take<double2>(ny * ne);
         d.M32 = want32 ? cv.take<float2>(ny * ne) : nullptr;
+        d.ML32 = want32 ? cv.take<float2>(ny * ne) : nullptr;
         d.D32 = c->opt.precision != EF_PREC_FP64 ? cv.take<float2>(ny * (size_t)eb.cap) : nullptr;
         d.E32 = c->opt.precision != EF_PREC_FP64 ? cv.take<uint16_t>(ny * (size_t)eb.cap) : nullptr;
         d.D64 = c->opt.precision != EF_PREC_FP32_MINOR ? cv.take<double2>(ny * (size_t)eb.cap) : nullptr;

@@ -103,7 +103,11 @@ __global__ void __launch_bounds__(128) k_build_branches(ExactBlockDev B0, ExactB
         for (int e = threadIdx.x; e < ne; e += blockDim.x) {
             const double2 v = cur[e];
             o64[e] = v;
-            if (want32) B.M32[(size_t)z * ne + e] = make_float2((float)v.x, (float)v.y);
+            if (want32) {
+                const float rh = (float)v.x, ih = (float)v.y;
+                B.M32[(size_t)z * ne + e] = make_float2(rh, ih);
+                B.ML32[(size_t)z * ne + e] = make_float2((float)(v.x - (double)rh), (float)(v.y - (double)ih));
+            }
         }
         __syncthreads();
     }
@@ -401,10 +405,6 @@ __device__ __forceinline__ float4 cf_shfl(float4 v, int src, int width) {
     return make_float4(__shfl_sync(full, v.x, src, width), __shfl_sync(full, v.y, src, width),
                        __shfl_sync(full, v.z, src, width), __shfl_sync(full, v.w, src, width));
 }
-__device__ __forceinline__ float4 cf_from_d(double2 a) {
-    const float rh = (float)a.x, ih = (float)a.y;
-    return make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
-}
 
 // A group of G lanes (G a power of two, eta <= G <= 32) factors one listed
 // minor; lane r holds row r (float pairs) and the rows never move: at step k
@@ -443,11 +443,18 @@ __global__ void __launch_bounds__(128) k_exact_lu_ffm(ExactBlockDev B0, ExactBlo
             row_idx = nth_row(bits[2 * pos], bits[2 * pos + 1], B.mask0, B.mask1, r, cnt);
         }
         const bool ok = valid && cnt == eta;
+        // the row as float pairs: leading parts from the FP32 branch matrix, the
+        // rest of the FP64 value from its companion (both written by the builder)
         float4 row[G];
-        const double2* src = B.M64 + ((size_t)z * B.n + (size_t)(row_idx < 0 ? 0 : row_idx)) * eta;
+        const size_t src = ((size_t)z * B.n + (size_t)(row_idx < 0 ? 0 : row_idx)) * eta;
 #pragma unroll
-        for (int j = 0; j < G; ++j)
-            row[j] = (ok && r < eta && j < eta) ? cf_from_d(src[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < G; ++j) {
+            row[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok && r < eta && j < eta) {
+                const float2 h = B.M32[src + j], l = B.ML32[src + j];
+                row[j] = make_float4(h.x, h.y, l.x, l.y);
+            }
+        }
         bool done = !ok || r >= eta;
         float4 d = make_float4(1.f, 0.f, 0.f, 0.f);
         int inv = 0;

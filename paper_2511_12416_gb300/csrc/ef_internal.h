@@ -41,6 +41,7 @@ struct ExactBlockDev {
     const uint32_t* F;      // L x n: flip masks over pattern bits
     double2* M64;           // 2^r x n x eta branch matrices (FP64)
     float2* M32;            // same, FP32 (may be null)
+    float2* ML32;           // with M32: M64 - M32 rounded to FP32 (M32 + ML32 = M64 to about 48 bits)
     // determinants per (bitstring column, pattern), [stride][2^r] each (dix):
     float2* D32;            // FP32 LU: det
     uint16_t* E32;          // FP32 LU: error term |det|^2 er2 + zabs2 as bfloat16 rounded up;
