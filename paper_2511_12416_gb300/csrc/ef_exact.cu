@@ -58,18 +58,153 @@ int sm_count() {
     return cached[dev];
 }
 
+// ---- float-pair ("double-float") arithmetic for the branch-matrix builder,
+// the transforms over FP32 determinants and the redo of listed determinants:
+// a value is hi + lo with |lo| <= ulp(hi)/2, about 48 bits.
+// Sums use the error-free two-sum (Knuth) and products the FMA residual
+// (Dekker's product with a fused multiply-add), each renormalised.
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 quick_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
+    const float2 s = two_sum(x.x, y.x);
+    return quick_two_sum(s.x, s.y + (x.y + y.y));
+}
+__device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 ff_mul(float2 x, float2 y) {
+    const float p = x.x * y.x;
+    const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));
+    return quick_two_sum(p, e);
+}
+// Complex float pairs as float4 (re hi, im hi, re lo, im lo): the leading
+// parts form one FP32 complex and the trailing parts another, so the real and
+// imaginary float-pair operations run as packed FP32x2 instructions, one
+// instruction for both (each component is rounded exactly as the scalar
+// operation would be).
+__device__ __forceinline__ float2 cf_re(float4 v) { return make_float2(v.x, v.z); }
+__device__ __forceinline__ float2 cf_im(float4 v) { return make_float2(v.y, v.w); }
+__device__ __forceinline__ float2 cf_hi(float4 v) { return make_float2(v.x, v.y); }  // leading parts (FP32 complex)
+__device__ __forceinline__ float4 cf_make(float2 re, float2 im) { return make_float4(re.x, im.x, re.y, im.y); }
+__device__ __forceinline__ float4 cf_from_f(float2 z) { return make_float4(z.x, z.y, 0.f, 0.f); }
+
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+__device__ __forceinline__ float2 p2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 p2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+#else
+__device__ __forceinline__ float2 p2_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 p2_mul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+#endif
+
+// Two float-pair additions at once: ff_add on (xh.x, xl.x) + (yh.x, yl.x) and
+// on the .y components, in ff_add's order of operations.
+__device__ __forceinline__ float4 cf_add(float4 a, float4 b) {
+    const float2 ah = make_float2(a.x, a.y), al = make_float2(a.z, a.w);
+    const float2 bh = make_float2(b.x, b.y), bl = make_float2(b.z, b.w);
+    const float2 s = p2_add(ah, bh);
+    const float2 bb = p2_sub(s, ah);
+    const float2 e = p2_add(p2_sub(ah, p2_sub(s, bb)), p2_sub(bh, bb));
+    const float2 t = p2_add(e, p2_add(al, bl));
+    const float2 r = p2_add(s, t);
+    const float2 lo = p2_sub(t, p2_sub(r, s));
+    return make_float4(r.x, r.y, lo.x, lo.y);
+}
+__device__ __forceinline__ float4 cf_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 cf_sub(float4 a, float4 b) { return cf_add(a, cf_neg(b)); }
+// Two float-pair products at once (ff_mul's order of operations).
+__device__ __forceinline__ float4 cf_mul2(float2 xh, float2 xl, float2 yh, float2 yl) {
+    const float2 p = p2_mul(xh, yh);
+    const float2 e = p2_fma(xh, yl, p2_fma(xl, yh, p2_fma(xh, yh, make_float2(-p.x, -p.y))));
+    const float2 s = p2_add(p, e);
+    const float2 lo = p2_sub(e, p2_sub(s, p));
+    return make_float4(s.x, s.y, lo.x, lo.y);
+}
+// complex product: (ar br, ar bi) + (-ai bi, ai br), as the scalar
+// ff_add(ff_mul(ar, br), -ff_mul(ai, bi)) and ff_add(ff_mul(ar, bi), ff_mul(ai, br))
+__device__ __forceinline__ float4 cf_mul(float4 a, float4 b) {
+    const float4 p1 = cf_mul2(make_float2(a.x, a.x), make_float2(a.z, a.z), make_float2(b.x, b.y),
+                              make_float2(b.z, b.w));
+    const float4 p2 = cf_mul2(make_float2(-a.y, a.y), make_float2(-a.w, a.w), make_float2(b.y, b.x),
+                              make_float2(b.w, b.z));
+    return cf_add(p1, p2);
+}
+
 // ---------------------------------------------------------------- 1. builder
 
 // Blocks B0 and B1 (blockIdx.y) in one launch: each is mostly latency at this
 // size, so two launches cost about twice one.
+//
+// With FP32 outputs wanted (every precision but EF_PREC_FP64) and at most
+// kBuildFFModes modes, the products run in float pairs (about 48 bits) on the
+// FP32 pipes instead of FP64 (an FP64 instruction costs a warp about 64 cycles
+// of its sub-partition's FP64 unit): M32 gets the leading parts, ML32 the
+// trailing ones, M64 their sum (used only by the whole-bitstring FP64 redo).
+// The plain FP64 form keeps FP64 products.
+constexpr int kBuildFFModes = 64;
+
+__device__ __forceinline__ float4 cf_of_d(double2 a) {
+    const float rh = (float)a.x, ih = (float)a.y;
+    return make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
+}
+
 __global__ void __launch_bounds__(128) k_build_branches(ExactBlockDev B0, ExactBlockDev B1, int want32) {
     extern __shared__ double2 smb[];
     const ExactBlockDev& B = blockIdx.y ? B1 : B0;
     const int n = B.n, eta = B.eta, ne = n * eta;
+    const uint32_t ny = 1u << B.r;
+    if (want32 && n <= kBuildFFModes) {
+        float4* cur = reinterpret_cast<float4*>(smb);
+        float4* nxt = cur + ne;
+        float4* Tf = nxt + ne;
+        int* sgn = reinterpret_cast<int*>(Tf + (size_t)n * n);
+        for (uint32_t z = blockIdx.x; z < ny; z += gridDim.x) {
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) cur[e] = cf_of_d(B.S0C[e]);
+            for (int l = 0; l < B.L; ++l) {
+                for (int m = threadIdx.x; m < n; m += blockDim.x) sgn[m] = __popc(z & B.F[l * n + m]) & 1;
+                const double2* T = B.T + (size_t)l * n * n;
+                for (int e = threadIdx.x; e < n * n; e += blockDim.x) Tf[e] = cf_of_d(T[e]);
+                __syncthreads();
+                for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                    const int i = e / eta, c = e - i * eta;
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int m = 0; m < n; ++m) {
+                        const float4 x = cur[m * eta + c];
+                        acc = cf_add(acc, cf_mul(Tf[i * n + m], sgn[m] ? cf_neg(x) : x));
+                    }
+                    nxt[e] = acc;
+                }
+                __syncthreads();
+                float4* tmp = cur;
+                cur = nxt;
+                nxt = tmp;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                const float4 v = cur[e];
+                const size_t o = (size_t)z * ne + e;
+                B.M32[o] = make_float2(v.x, v.y);
+                B.ML32[o] = make_float2(v.z, v.w);
+                B.M64[o] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+            }
+            __syncthreads();
+        }
+        return;
+    }
     double2* bufA = smb;
     double2* bufB = smb + ne;
     int* sgn = reinterpret_cast<int*>(smb + 2 * ne);
-    const uint32_t ny = 1u << B.r;
     for (uint32_t z = blockIdx.x; z < ny; z += gridDim.x) {
         double2* cur = bufA;
         double2* nxt = bufB;
@@ -121,6 +256,8 @@ cudaError_t launch_build_branches(const ExactBlockDev& b0, const ExactBlockDev& 
     for (int i = 0; i < nblk; ++i) {
         const ExactBlockDev& b = i ? b1 : b0;
         smem = std::max(smem, (size_t)2 * b.n * b.eta * sizeof(double2) + (size_t)b.n * sizeof(int));
+        if (want32 && b.n <= kBuildFFModes)  // float-pair path: the layer's T staged as float pairs too
+            smem = std::max(smem, (size_t)(2 * b.n * b.eta + b.n * b.n) * sizeof(float4) + (size_t)b.n * sizeof(int));
         ny = std::max(ny, 1u << b.r);
     }
     cudaError_t e = raise_dynamic_smem((const void*)k_build_branches, smem);
@@ -300,88 +437,6 @@ cudaError_t launch_exact_lu_f64(const ExactBlockDev& b, const uint64_t* bits, in
 
 __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// ---- float-pair ("double-float") arithmetic for the transform path over FP32
-// determinants: a value is hi + lo with |lo| <= ulp(hi)/2, about 48 bits.
-// Sums use the error-free two-sum (Knuth) and products the FMA residual
-// (Dekker's product with a fused multiply-add), each renormalised.
-
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    return make_float2(s, (a - (s - bb)) + (b - bb));
-}
-__device__ __forceinline__ float2 quick_two_sum(float a, float b) {  // |a| >= |b|
-    const float s = a + b;
-    return make_float2(s, b - (s - a));
-}
-__device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
-    const float2 s = two_sum(x.x, y.x);
-    return quick_two_sum(s.x, s.y + (x.y + y.y));
-}
-__device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
-__device__ __forceinline__ float2 ff_mul(float2 x, float2 y) {
-    const float p = x.x * y.x;
-    const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));
-    return quick_two_sum(p, e);
-}
-// Complex float pairs as float4 (re hi, im hi, re lo, im lo): the leading
-// parts form one FP32 complex and the trailing parts another, so the real and
-// imaginary float-pair operations run as packed FP32x2 instructions, one
-// instruction for both (each component is rounded exactly as the scalar
-// operation would be).
-__device__ __forceinline__ float2 cf_re(float4 v) { return make_float2(v.x, v.z); }
-__device__ __forceinline__ float2 cf_im(float4 v) { return make_float2(v.y, v.w); }
-__device__ __forceinline__ float2 cf_hi(float4 v) { return make_float2(v.x, v.y); }  // leading parts (FP32 complex)
-__device__ __forceinline__ float4 cf_make(float2 re, float2 im) { return make_float4(re.x, im.x, re.y, im.y); }
-__device__ __forceinline__ float4 cf_from_f(float2 z) { return make_float4(z.x, z.y, 0.f, 0.f); }
-
-#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
-__device__ __forceinline__ float2 p2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
-__device__ __forceinline__ float2 p2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-#else
-__device__ __forceinline__ float2 p2_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 p2_mul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) {
-    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
-}
-#endif
-
-// Two float-pair additions at once: ff_add on (xh.x, xl.x) + (yh.x, yl.x) and
-// on the .y components, in ff_add's order of operations.
-__device__ __forceinline__ float4 cf_add(float4 a, float4 b) {
-    const float2 ah = make_float2(a.x, a.y), al = make_float2(a.z, a.w);
-    const float2 bh = make_float2(b.x, b.y), bl = make_float2(b.z, b.w);
-    const float2 s = p2_add(ah, bh);
-    const float2 bb = p2_sub(s, ah);
-    const float2 e = p2_add(p2_sub(ah, p2_sub(s, bb)), p2_sub(bh, bb));
-    const float2 t = p2_add(e, p2_add(al, bl));
-    const float2 r = p2_add(s, t);
-    const float2 lo = p2_sub(t, p2_sub(r, s));
-    return make_float4(r.x, r.y, lo.x, lo.y);
-}
-__device__ __forceinline__ float4 cf_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
-__device__ __forceinline__ float4 cf_sub(float4 a, float4 b) { return cf_add(a, cf_neg(b)); }
-// Two float-pair products at once (ff_mul's order of operations).
-__device__ __forceinline__ float4 cf_mul2(float2 xh, float2 xl, float2 yh, float2 yl) {
-    const float2 p = p2_mul(xh, yh);
-    const float2 e = p2_fma(xh, yl, p2_fma(xl, yh, p2_fma(xh, yh, make_float2(-p.x, -p.y))));
-    const float2 s = p2_add(p, e);
-    const float2 lo = p2_sub(e, p2_sub(s, p));
-    return make_float4(s.x, s.y, lo.x, lo.y);
-}
-// complex product: (ar br, ar bi) + (-ai bi, ai br), as the scalar
-// ff_add(ff_mul(ar, br), -ff_mul(ai, bi)) and ff_add(ff_mul(ar, bi), ff_mul(ai, br))
-__device__ __forceinline__ float4 cf_mul(float4 a, float4 b) {
-    const float4 p1 = cf_mul2(make_float2(a.x, a.x), make_float2(a.z, a.z), make_float2(b.x, b.y),
-                              make_float2(b.z, b.w));
-    const float4 p2 = cf_mul2(make_float2(-a.y, a.y), make_float2(-a.w, a.w), make_float2(b.y, b.x),
-                              make_float2(b.w, b.z));
-    return cf_add(p1, p2);
 }
 
 // ---- float-pair LU for the listed determinants of EF_PREC_AUTO (the FP32
