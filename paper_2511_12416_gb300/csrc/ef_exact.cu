@@ -160,6 +160,7 @@ __device__ __forceinline__ float4 cf_of_d(double2 a) {
 }
 
 __global__ void __launch_bounds__(128) k_build_branches(ExactBlockDev B0, ExactBlockDev B1, int want32) {
+    cudaGridDependencySynchronize();  // see launch_pdl
     extern __shared__ double2 smb[];
     const ExactBlockDev& B = blockIdx.y ? B1 : B0;
     const int n = B.n, eta = B.eta, ne = n * eta;
@@ -263,7 +264,8 @@ cudaError_t launch_build_branches(const ExactBlockDev& b0, const ExactBlockDev& 
     cudaError_t e = raise_dynamic_smem((const void*)k_build_branches, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid(std::min<uint32_t>(ny, (uint32_t)sm_count() * 16u), (unsigned)nblk);
-    k_build_branches<<<grid, 128, smem, s>>>(b0, nblk == 2 ? b1 : b0, want32 ? 1 : 0);
+    const cudaError_t le = launch_pdl(k_build_branches, grid, dim3(128), smem, s, b0, nblk == 2 ? b1 : b0, want32 ? 1 : 0);
+    if (le != cudaSuccess) return le;
     st.launches += 1;
     return cudaGetLastError();
 }
@@ -278,6 +280,7 @@ template <int ETA>
 __global__ void __launch_bounds__(128) k_exact_lu_f64t(ExactBlockDev B, const uint64_t* __restrict__ bits,
                                                        int64_t nb, const int* __restrict__ list,
                                                        const int* __restrict__ list_count, int64_t stride) {
+    cudaGridDependencySynchronize();  // see launch_pdl
     const int64_t count = list ? (int64_t)(*list_count) : nb;
     const int64_t total = count << B.r;
     const int n = B.n;
@@ -307,7 +310,8 @@ static cudaError_t launch_f64t_eta(const ExactBlockDev& b, const uint64_t* bits,
     // list mode: the list is usually short or empty, so a small grid strides over it
     const int64_t items = (list ? stride : nb) << b.r;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, list ? sm_count() * 4 : sm_count() * 32));
-    k_exact_lu_f64t<ETA><<<(unsigned)blocks, 128, 0, s>>>(b, bits, nb, list, list_count, stride);
+    const cudaError_t le = launch_pdl(k_exact_lu_f64t<ETA>, dim3((unsigned)blocks), dim3(128), 0, s, b, bits, nb, list, list_count, stride);
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 
@@ -473,6 +477,7 @@ __global__ void __launch_bounds__(128) k_exact_lu_ffm(ExactBlockDev B0, ExactBlo
                                                       const int2* __restrict__ mlist0,
                                                       const int2* __restrict__ mlist1,
                                                       const int* __restrict__ mcount) {
+    cudaGridDependencySynchronize();  // see launch_pdl
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int r = lane & (G - 1);
@@ -568,10 +573,12 @@ cudaError_t launch_exact_lu_redo_minors(const ExactBlockDev& b0, const ExactBloc
     // the count lives on the device: a fixed grid of one wave strides over the list
     const int grid = sm_count() * 4;
     const int eta = b0.eta;
-    if (eta <= 2) k_exact_lu_ffm<2><<<grid, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount);
-    else if (eta <= 4) k_exact_lu_ffm<4><<<grid, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount);
-    else if (eta <= 8) k_exact_lu_ffm<8><<<grid, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount);
-    else k_exact_lu_ffm<16><<<grid, 128, 0, s>>>(b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    cudaError_t le;
+    if (eta <= 2) le = launch_pdl(k_exact_lu_ffm<2>, dim3(grid), dim3(128), 0, s, b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    else if (eta <= 4) le = launch_pdl(k_exact_lu_ffm<4>, dim3(grid), dim3(128), 0, s, b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    else if (eta <= 8) le = launch_pdl(k_exact_lu_ffm<8>, dim3(grid), dim3(128), 0, s, b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    else le = launch_pdl(k_exact_lu_ffm<16>, dim3(grid), dim3(128), 0, s, b0, b1, nblk, bits, mlist0, mlist1, mcount);
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 
@@ -701,6 +708,7 @@ __global__ void __launch_bounds__(256, 3) k_exact_combine(ExactCombineDev C, con
                                                        const int* __restrict__ list_count, double* __restrict__ out,
                                                        double* __restrict__ err, int* __restrict__ append_list,
                                                        int* __restrict__ append_count) {
+    cudaGridDependencySynchronize();  // see launch_pdl
     constexpr int NT = 256;
     constexpr int NW = NT / 32;
     // dynamic shared memory: [F_0 (2^r_0), F_1 (2^r_1), 16 bytes each, when C.wht:
@@ -966,6 +974,7 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
                                                              double* __restrict__ out, double* __restrict__ err,
                                                              int* __restrict__ append_list,
                                                              int* __restrict__ append_count) {
+    cudaGridDependencySynchronize();  // see launch_pdl
     constexpr int NW = NT / 32;
     extern __shared__ float4 smF[];
     __shared__ float4 redf[2][NW];
@@ -1180,6 +1189,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
                                                           double* __restrict__ out, double* __restrict__ err,
                                                           int* __restrict__ append_list,
                                                           int* __restrict__ append_count) {
+    cudaGridDependencySynchronize();  // see launch_pdl
     constexpr int NL = 1 << RL;  // RPL: rows per lane at most
     extern __shared__ float4 smWp[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1418,8 +1428,9 @@ static cudaError_t launch_wp_r(const ExactCombineDev& c, size_t per_warp, const 
     cudaError_t e = raise_dynamic_smem((const void*)k_exact_combine_wp<RL, RPL>, smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nb + 3) / 4, (int64_t)sm_count() * 8));
-    k_exact_combine_wp<RL, RPL><<<(unsigned)blocks, 128, smem, s>>>(c, bits, nb, stride, list, list_count, out, err,
-                                                                    append_list, append_count);
+    e = launch_pdl(k_exact_combine_wp<RL, RPL>, dim3((unsigned)blocks), dim3(128), smem, s, c, bits, nb, stride, list,
+                   list_count, out, err, append_list, append_count);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1467,8 +1478,9 @@ cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits,
         cudaError_t e = raise_dynamic_smem((const void*)k_exact_combine_ffr<NT>, smem);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * 12));
-        k_exact_combine_ffr<NT><<<(unsigned)blocks, NT, smem, s>>>(c, bits, nb, stride, list, list_count, out, err,
-                                                                   append_list, append_count);
+        e = launch_pdl(k_exact_combine_ffr<NT>, dim3((unsigned)blocks), dim3(NT), smem, s, c, bits, nb, stride, list,
+                       list_count, out, err, append_list, append_count);
+        if (e != cudaSuccess) return e;
         st.launches += 1;
         return cudaGetLastError();
     }
@@ -1476,8 +1488,9 @@ cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits,
     cudaError_t e = raise_dynamic_smem((const void*)k_exact_combine, smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * 16));
-    k_exact_combine<<<(unsigned)blocks, 256, smem, s>>>(c, bits, nb, stride, list, list_count, out, err, append_list,
-                                                        append_count);
+    e = launch_pdl(k_exact_combine, dim3((unsigned)blocks), dim3(256), smem, s, c, bits, nb, stride, list, list_count,
+                   out, err, append_list, append_count);
+    if (e != cudaSuccess) return e;
     st.launches += 1;
     return cudaGetLastError();
 }

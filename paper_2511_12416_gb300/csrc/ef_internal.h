@@ -185,6 +185,29 @@ int sm_count();
 // re-checks each node against the current limit then fails that node).
 cudaError_t raise_dynamic_smem(const void* kernel, size_t bytes);
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the previous kernel on the stream is still finishing, which hides the
+// launch latency between the dependent kernels of a call. Every kernel
+// launched this way calls cudaGridDependencySynchronize() before its first
+// global-memory access, so it still sees all of the previous kernel's writes
+// (and writes nothing the previous kernel reads) exactly as with an ordinary
+// launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // branch matrices of nblk (1 or 2) mode blocks in one launch
 cudaError_t launch_build_branches(const ExactBlockDev& b0, const ExactBlockDev& b1, int nblk, bool want32,
                                   cudaStream_t s, LaunchStats& st);

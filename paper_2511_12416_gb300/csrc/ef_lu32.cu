@@ -31,6 +31,7 @@ int exact_f32_chunk_log2(int n, int eta, int r, int64_t nb) {
 template <int ETA>
 __global__ void __launch_bounds__(128) k_exact_lu_f32(ExactBlockDev B0, ExactBlockDev B1,
                                                       const uint64_t* __restrict__ bits, int64_t nb) {
+    cudaGridDependencySynchronize();  // see launch_pdl
     extern __shared__ float2 smM[];
     // both mode blocks in one launch (blockIdx.z): one tail instead of two
     const ExactBlockDev& B = blockIdx.z ? B1 : B0;
@@ -96,7 +97,8 @@ static cudaError_t launch_f32_eta(const ExactBlockDev& b0, const ExactBlockDev& 
     cudaError_t e = raise_dynamic_smem((const void*)k_exact_lu_f32<ETA>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((nb + 127) / 128), (unsigned)std::min(chunks, 65535), (unsigned)nblk);
-    k_exact_lu_f32<ETA><<<grid, 128, smem, s>>>(b0, nblk == 2 ? b1 : b0, bits, nb);
+    e = launch_pdl(k_exact_lu_f32<ETA>, grid, dim3(128), smem, s, b0, nblk == 2 ? b1 : b0, bits, nb);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
