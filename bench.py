@@ -59,9 +59,9 @@ NB = 10_000
 # -k regex:"k_exact|k_build"` on `bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-fp64-form
 # --no-secondary`; ncu empties the caches before each launch): one launch covers both mode blocks;
 # of the 51 MB of FP32 results (float2 value + bfloat16 error term per minor) it writes, about
-# 2.3 MB reach DRAM within the launch and the rest stays in L2 until the combine; the pattern
-# matrices and bitstrings are read cold (2.3 MB). To be re-measured whenever that kernel changes.
-LU_DRAM_BYTES_PER_LAUNCH = 4_600_747  # mean of the last three launches (4.56, 4.61, 4.63 MB)
+# 1.4 MB reach DRAM within the launch and the rest stays in L2 until the combine; the pattern
+# matrices and bitstrings are read cold (2.0 MB). To be re-measured whenever that kernel changes.
+LU_DRAM_BYTES_PER_LAUNCH = 3_425_109  # mean of the last three launches (3.44, 3.41, 3.42 MB)
 L2_BYTES = 129 * 2 ** 20
 WORKLOAD = ("LUCJ exact: 2x16 modes (32 qubits), 8a+8b, k=16 controlled-phase gates "
             "(4 aa + 4 bb neighbour, 8 ab on-site, N(0,0.1)), 2^16 branches, 10^4 sector bitstrings")
