@@ -309,7 +309,7 @@ static cudaError_t launch_f64t_eta(const ExactBlockDev& b, const uint64_t* bits,
                                    const int* list_count, int64_t stride, cudaStream_t s) {
     // list mode: the list is usually short or empty, so a small grid strides over it
     const int64_t items = (list ? stride : nb) << b.r;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, list ? sm_count() * 4 : sm_count() * 32));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, list ? sm_count() : sm_count() * 32));
     const cudaError_t le = launch_pdl(k_exact_lu_f64t<ETA>, dim3((unsigned)blocks), dim3(128), 0, s, b, bits, nb, list, list_count, stride);
     if (le != cudaSuccess) return le;
     return cudaGetLastError();
@@ -1487,7 +1487,8 @@ cudaError_t launch_exact_combine(const ExactCombineDev& c, const uint64_t* bits,
     const size_t smem = exact_combine_smem(c);
     cudaError_t e = raise_dynamic_smem((const void*)k_exact_combine, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * 16));
+    // a list (the FP64 pass over the results still above tol) is usually short or empty
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * (list ? 4 : 16)));
     e = launch_pdl(k_exact_combine, dim3((unsigned)blocks), dim3(256), smem, s, c, bits, nb, stride, list, list_count,
                    out, err, append_list, append_count);
     if (e != cudaSuccess) return e;
