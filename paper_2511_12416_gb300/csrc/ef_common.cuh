@@ -81,7 +81,7 @@ template <typename R> __device__ __forceinline__ R pivot_err_term(R t) {
 // 2^-7 above it). An infinite or undefined term (0 x inf after a vanishing
 // pivot) is taken as the largest float, an error too large to bound. The sign
 // bit is never set here: a set sign bit (kErrRedone) marks a determinant whose
-// value was redone in FP64.
+// value was redone (in float pairs).
 __device__ __forceinline__ uint16_t err_term_code(float2 det, float er2, float zabs2) {
     float t = fmaf(fmaf(det.x, det.x, det.y * det.y), er2, zabs2);
     t = t <= 3.0e38f ? t : 3.0e38f;
@@ -90,7 +90,7 @@ __device__ __forceinline__ uint16_t err_term_code(float2 det, float er2, float z
 }
 constexpr uint16_t kErrRedone = 0xbf80u;  // -1 as a bfloat16
 __device__ __forceinline__ bool err_redone(uint16_t e) { return (e & 0x8000u) != 0u; }
-// the error term (0 for a determinant redone in FP64)
+// the error term (0 for a redone determinant)
 __device__ __forceinline__ float err_term_value(uint16_t e) {
     return err_redone(e) ? 0.f : __uint_as_float((uint32_t)e << 16);
 }

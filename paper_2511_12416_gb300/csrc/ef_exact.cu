@@ -12,7 +12,8 @@
 // once instead of the 2^{k_B} bit vectors, and the host folds the branch
 // weights w(x) onto patterns. Per block:
 //
-//   1. k_build_branches : U_B(z)[:, C_B] for every pattern z (dense FP64 products);
+//   1. k_build_branches : U_B(z)[:, C_B] for every pattern z (dense products, FP64 or
+//                         float pairs);
 //   2. k_exact_lu_*     : det U_B(z)[R_B(b), C_B] (Eq. 3) for every (pattern, bitstring),
 //                         LU with partial pivoting, plus a rounding-error proxy
 //                         (the FP32 kernels are in ef_lu32.cu);
@@ -628,8 +629,8 @@ __device__ __forceinline__ double neg_abs_int(double x) {
 }
 
 // Determinant z of block B for D column col, as the combine's source says. A
-// determinant redone in FP64 for a marked FP32 entry is stored as a float
-// pair (re hi, im hi, re lo, im lo) in its D64 slot.
+// determinant redone for a marked FP32 entry is stored as a float pair
+// (re hi, im hi, re lo, im lo) in its D64 slot.
 __device__ __forceinline__ double2 det_at(const ExactCombineDev& C, int B, size_t idx) {
     if (C.src == 1) return C.D64[B][idx];
     if (C.src == 2 && err_redone(C.E32[B][idx])) {
@@ -639,7 +640,7 @@ __device__ __forceinline__ double2 det_at(const ExactCombineDev& C, int B, size_
     const float2 v = C.D32[B][idx];
     return make_double2((double)v.x, (double)v.y);
 }
-// the stored error term of an FP32 determinant (0 for one redone in FP64)
+// the stored error term of an FP32 determinant (0 for a redone one)
 __device__ __forceinline__ float err_term(const ExactCombineDev& C, int B, size_t idx) {
     return err_term_value(C.E32[B][idx]);
 }
@@ -1136,7 +1137,7 @@ __global__ void __launch_bounds__(NT, 3) k_exact_combine_ffr(ExactCombineDev C, 
         if (budget >= 0.f) {
             // the largest threshold t whose terms <= t sum to at most the budget
             // (bisection on the bit patterns of non-negative floats); the
-            // determinants with larger terms are redone in FP64
+            // determinants with larger terms are redone in float pairs
             uint32_t lo = 0u, hi = 0x7f800000u;  // [0, +inf]
             while (hi - lo > 1u) {
                 const uint32_t mid = lo + ((hi - lo) >> 1);
@@ -1383,7 +1384,7 @@ __global__ void __launch_bounds__(128, (RL >= 5 ? 2 : 3)) k_exact_combine_wp(Exa
         if (budget >= 0.f) {
             __syncwarp();
             // the largest threshold whose terms sum to at most the budget, by
-            // bisection on float bit patterns; larger terms are redone in FP64
+            // bisection on float bit patterns; larger terms are redone in float pairs
             uint32_t lo = 0u, hi = 0x7f800000u;
             while (hi - lo > 1u) {
                 const uint32_t mid = lo + ((hi - lo) >> 1);
