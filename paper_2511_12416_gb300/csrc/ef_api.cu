@@ -1763,6 +1763,16 @@ int estimate_host(ef_circuit* c, const uint64_t* bits, int64_t nb, double eps, d
 
 // Host-pointer form of a *_dev call: bitstrings in, up to three per-bitstring
 // outputs back (out2, out3 nullable), on the circuit's own stream.
+int check_bits_host(const ef_circuit* c, const uint64_t* bits, int64_t nb) {
+    uint64_t hi[2] = {0, 0};
+    if (c->n < 64) hi[0] = ~0ull << c->n, hi[1] = ~0ull;
+    else if (c->n < 128) hi[1] = ~0ull << (c->n - 64);
+    for (int64_t i = 0; i < nb; ++i)
+        if ((bits[2 * i] & hi[0]) || (bits[2 * i + 1] & hi[1]))
+            return fail(EF_EINVAL, "bitstring " + std::to_string(i) + " has a bit at or above n_modes");
+    return EF_OK;
+}
+
 template <typename F>
 int host_call(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, double* out2, double* out3,
               F&& dev_call) {
@@ -1778,6 +1788,15 @@ int host_call(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, doub
     double* d3 = out3 ? d0 + 2 * nb : nullptr;
     int rc = dev_call(c->dBits.as<uint64_t>(), d0, d2, d3, s);
     if (rc) return rc;
+    // the host-side argument check runs while the GPU works (the kernels only
+    // read the bits through the blocks' mode masks, so a bit at or above n
+    // cannot make them access memory out of range); on failure nothing is
+    // copied back
+    rc = check_bits_host(c, bits, nb);
+    if (rc) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
     if (nb > 0) {
         EF_CK(cudaMemcpyAsync(out, d0, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
         if (out2) EF_CK(cudaMemcpyAsync(out2, d2, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1787,15 +1806,6 @@ int host_call(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, doub
     return EF_OK;
 }
 
-int check_bits_host(const ef_circuit* c, const uint64_t* bits, int64_t nb) {
-    uint64_t hi[2] = {0, 0};
-    if (c->n < 64) hi[0] = ~0ull << c->n, hi[1] = ~0ull;
-    else if (c->n < 128) hi[1] = ~0ull << (c->n - 64);
-    for (int64_t i = 0; i < nb; ++i)
-        if ((bits[2 * i] & hi[0]) || (bits[2 * i + 1] & hi[1]))
-            return fail(EF_EINVAL, "bitstring " + std::to_string(i) + " has a bit at or above n_modes");
-    return EF_OK;
-}
 
 }  // namespace
 
@@ -1936,8 +1946,6 @@ int ef_prob_exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double*
 int ef_prob_exact(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, double* err_out) {
     if (!c) return fail(EF_EINVAL, "NULL circuit");
     if (nb < 0 || (nb > 0 && (!bits || !out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
-    int rc = check_bits_host(c, bits, nb);
-    if (rc) return rc;
     return host_call(c, bits, nb, out, err_out, nullptr,
                      [&](const uint64_t* db, double* dout, double* derr, double*, cudaStream_t s) {
                          return ef_prob_exact_dev(c, db, nb, dout, derr, s);
@@ -1955,8 +1963,6 @@ int ef_prob_approx(ef_circuit* c, const uint64_t* bits, int64_t nb, int64_t n_tr
                    uint64_t index_base, double* out, double* stderr_out, double* err_out) {
     if (!c) return fail(EF_EINVAL, "NULL circuit");
     if (nb < 0 || (nb > 0 && (!bits || !out))) return fail(EF_EINVAL, "bad bitstring/output arguments");
-    int rc = check_bits_host(c, bits, nb);
-    if (rc) return rc;
     return host_call(c, bits, nb, out, stderr_out, err_out,
                      [&](const uint64_t* db, double* dout, double* dse, double* derr, cudaStream_t s) {
                          return ef_prob_approx_dev(c, db, nb, n_traj, seed, index_base, dout, dse, derr, s);
