@@ -47,13 +47,17 @@ cudaError_t raise_dynamic_smem(const void* kernel, size_t bytes) {
     return e;
 }
 
+// Streaming multiprocessors of the current device (queried once per device).
+// It only sizes grids: if the query fails, the launch that follows fails too,
+// so the fallback value merely keeps the grid arithmetic defined.
 int sm_count() {
+    constexpr int kFallback = 128;
     static int cached[64] = {};
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kFallback;
     if (cached[dev] <= 0) {
         int v = 0;
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = kFallback;
         cached[dev] = v;
     }
     return cached[dev];
