@@ -35,6 +35,10 @@
  *   - A bitstring whose Hamming weight (or, when the circuit splits into
  *     independent mode blocks, whose weight inside a block) differs from the
  *     initial state's gets probability 0 exactly; that is not an error.
+ *     A bit at or above n_modes is: the host-pointer calls return EF_EINVAL
+ *     and leave the outputs untouched (the *_dev calls do not inspect the
+ *     bits on the host; the kernels read them only through the circuit's
+ *     mode masks).
  *   - Angles: the differentiable angle vector lists, per gate in circuit order,
  *     Givens -> (theta, phi), PHASE -> phi, CPHASE -> theta.
  *
