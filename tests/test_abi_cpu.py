@@ -87,3 +87,31 @@ def test_angle_layout_and_extent_match_oracle(ef):
 
 def test_destroy_null_is_ok(ef):
     ef.load().ef_circuit_destroy(None)
+
+
+def test_missing_library_raises(ef, tmp_path):
+    """No CPU fallback: loading a library that is not there raises."""
+    import subprocess
+    import sys
+    missing = str(tmp_path / "libextraferm.so")
+    code = ("import paper_2511_12416_gb300 as ef\n"
+            f"try:\n    ef.load({missing!r})\nexcept OSError:\n    print('raised')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == "raised"
+
+
+def test_product_code_does_not_reach_the_oracle():
+    """The library, its binding and the input generators neither import nor
+    name the oracle package (only the tests, smoke() and the bench's CPU legs
+    may)."""
+    pat = re.compile(r"^\s*(?:from\s+oracle\b|import\s+oracle\b)|extraferm_oracle|[\'\"]oracle[\'\"]", re.M)
+    offenders = []
+    for sub in ("paper_2511_12416_gb300", "workloads", "include"):
+        for dirpath, _dirs, files in os.walk(os.path.join(ROOT, sub)):
+            for f in files:
+                if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                    p = os.path.join(dirpath, f)
+                    if pat.search(open(p, encoding="utf-8").read()):
+                        offenders.append(os.path.relpath(p, ROOT))
+    assert offenders == []
