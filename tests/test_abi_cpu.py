@@ -115,3 +115,17 @@ def test_product_code_does_not_reach_the_oracle():
                     if pat.search(open(p, encoding="utf-8").read()):
                         offenders.append(os.path.relpath(p, ROOT))
     assert offenders == []
+
+
+def test_oracle_does_not_reach_the_library():
+    """The oracle is independent of the CUDA path: it neither imports the
+    package nor loads its shared library."""
+    pat = re.compile(r"paper_2511_12416_gb300|libextraferm|ctypes", re.M)
+    offenders = []
+    for dirpath, _dirs, files in os.walk(os.path.join(ROOT, "oracle")):
+        for f in files:
+            if f.endswith((".py", ".c", ".h")):
+                p = os.path.join(dirpath, f)
+                if pat.search(open(p, encoding="utf-8").read()):
+                    offenders.append(os.path.relpath(p, ROOT))
+    assert offenders == []
