@@ -74,6 +74,23 @@ MUTANTS = [
     ("derivative of cos(theta/4) with the wrong sign", EO,
      '-cp["s"] / 4.0', 'cp["s"] / 4.0',
      ["fd_gradient", "sv_derivative"]),
+    ("product rule without the segment's own derivative", EO,
+     "dseg = dG @ seg + G @ dseg", "dseg = dG @ seg",
+     ["fd_gradient", "sv_derivative"]),
+    ("derivative of D_x with theta/4 instead of theta/2", EO,
+     'dd_coef[:, cp["p"]] += 0.5j * v', 'dd_coef[:, cp["p"]] += 0.25j * v',
+     # in the gradient pin's circuit a phase on those modes only changes the amplitude's phase:
+     # the amplitude derivative sees it, the probability derivative cannot
+     ["sv_derivative"]),
+    ("determinant derivative keeping only the last column", EO,
+     "out += np.linalg.det(Ai)", "out = np.linalg.det(Ai)",
+     ["fd_gradient", "sv_derivative"]),
+    ("derivative of the global phase with the wrong sign", EO,
+     "dphase = -0.25j * sum(", "dphase = 0.25j * sum(",
+     ["sv_derivative"]),
+    ("Estimate rounds that never tighten p_max", EO,
+     "pmax[i] = min(pmax[i], ph[i] + eps_r)", "pmax[i] = pmax[i]",
+     ["estimate_eps"]),
     ("SplitMix64 multiplier off by one", EO,
      "0xBF58476D1CE4E5B9", "0xBF58476D1CE4E5B8",
      ["splitmix64"]),
@@ -116,6 +133,7 @@ def _pins():
         "eq6_limits": PINS.test_trajectory_bound_eq6_limits_and_monotonicity,
         "splitmix64": PINS.test_splitmix64_known_answers,
         "trajectory_grid": PINS.test_trajectory_grid,
+        "estimate_eps": PINS.test_estimate_oracle_meets_eps,
         "raw_zero_angles": PINS.test_raw_estimate_zero_angles_is_exact,
         "raw_unbiased": PINS.test_raw_estimate_unbiased_amplitude_and_exact_bias_formula,
         "raw_converges": PINS.test_raw_estimate_converges_and_stderr_is_calibrated,
