@@ -65,8 +65,11 @@ MUTANTS = [
      'cp["c"] / cp["pT0"]', 'cp["c"] / max(cp["pT1"], 1e-300)',
      ["raw_zero_angles", "raw_unbiased", "raw_converges"]),
     ("standard error without the factor 2 (delta method for |alpha|^2)", EO,
-     "stderr[i] = 2.0 * math.sqrt(", "stderr[i] = 0.5 * math.sqrt(",
-     ["raw_converges"]),
+     "stderr[i] = 2.0 * math.sqrt(", "stderr[i] = 1.0 * math.sqrt(",
+     ["stderr_spread"]),
+    ("standard error twice too large", EO,
+     "stderr[i] = 2.0 * math.sqrt(", "stderr[i] = 4.0 * math.sqrt(",
+     ["stderr_spread"]),
     ("global phase e^{+i theta/4}", EO,
      "np.exp(-1j * sum(cp[\"theta\"] for cp in self.cps) / 4.0)",
      "np.exp(1j * sum(cp[\"theta\"] for cp in self.cps) / 4.0)",
@@ -137,6 +140,7 @@ def _pins():
         "raw_zero_angles": PINS.test_raw_estimate_zero_angles_is_exact,
         "raw_unbiased": PINS.test_raw_estimate_unbiased_amplitude_and_exact_bias_formula,
         "raw_converges": PINS.test_raw_estimate_converges_and_stderr_is_calibrated,
+        "stderr_spread": PINS.test_raw_estimate_stderr_matches_spread_over_seeds,
         "fd_gradient": PINS.test_forward_mode_gradient_matches_central_differences,
         "sv_derivative": PINS.test_forward_mode_derivative_of_amplitude_matches_statevector_differences,
     }
