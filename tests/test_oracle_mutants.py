@@ -70,6 +70,13 @@ MUTANTS = [
     ("standard error twice too large", EO,
      "stderr[i] = 2.0 * math.sqrt(", "stderr[i] = 4.0 * math.sqrt(",
      ["stderr_spread"]),
+    ("p_hat as the mean of |Y|^2 instead of |mean Y|^2 (Section III-A)", EO,
+     "p_hat[i] = abs(a) ** 2", "p_hat[i] = float(np.mean(np.abs(Y) ** 2))",
+     ["raw_unbiased", "raw_converges"]),
+    ("branch weights and thresholds from the unwrapped angle", EO,
+     'th = wrap_angle(float(g["theta"]))', 'th = float(g["theta"])',
+     # Eq. 7 holds for every real theta, so Exact results cannot see this; the thresholds can
+     ["thresholds"]),
     ("global phase e^{+i theta/4}", EO,
      "np.exp(-1j * sum(cp[\"theta\"] for cp in self.cps) / 4.0)",
      "np.exp(1j * sum(cp[\"theta\"] for cp in self.cps) / 4.0)",
