@@ -80,6 +80,31 @@ def test_approx_global_index_and_subsets(lib):
     assert np.array_equal(p_sub, p_all[30:45]) and np.array_equal(se_sub, se_all[30:45])
 
 
+def test_approx_global_indices_across_2_32(lib):
+    """Global bitstring indices that cross 2^32: the high index word of the
+    Philox counter reaches the trajectories as in the oracle (same
+    trajectories, FP64 parity), and the indices, not the positions in the
+    call, select them."""
+    c = W.random_fig4_circuit(10, 4, 7, 3, seed=31, angle_std=1.2)
+    bits = W.sector_bitstrings_all(10, 4)
+    sub = bits[np.argsort(-O.exact_probabilities(c, bits))[:20]]  # the 20 most probable outcomes
+    base = (1 << 32) - 9
+    seed, t = 0x0123_4567_89AB_CDEF, 700
+    idx = [base + i for i in range(len(sub))]
+    p_ref, se_ref = O.raw_estimate(c, sub, t=t, seed=seed, b_indices=idx)
+    floor = 1e-6 / math.comb(c.n_modes, len(c.occupied_modes()))
+    for prec, tol in ((lib.EF_PREC_FP64, 1e-10), (lib.EF_PREC_AUTO, 1e-5)):
+        p, se, _ = run_approx(lib, c, sub, t, seed, prec, index_base=base)
+        assert np.max(np.abs(p - p_ref) / np.maximum(p_ref, floor)) <= tol, prec
+        assert np.max(np.abs(se - se_ref) / np.maximum(se_ref, floor)) <= (1e-8 if tol < 1e-9 else 1e-3), prec
+    # bitstrings 9.. sit at indices 2^32 + 0.., which share their low words with indices 0..
+    p_low, _, _ = run_approx(lib, c, sub[9:], t, seed, lib.EF_PREC_FP64, index_base=0)
+    p_low_ref, _ = O.raw_estimate(c, sub[9:], t=t, seed=seed)
+    assert np.max(np.abs(p_low - p_low_ref) / np.maximum(p_low_ref, floor)) <= 1e-10
+    # ... and their trajectories differ: the GPU matched both sets, so it keeps the high word
+    assert np.max(np.abs(p_low_ref - p_ref[9:]) / np.maximum(p_ref[9:], floor)) > 1e-3
+
+
 def test_approx_zero_angles_is_exact(lib):
     c, bits = W.brick8_exact()
     recs = [(int(g["kind"]), int(g["p"]), int(g["q"]), 0.0 if int(g["kind"]) == W.CPHASE else float(g["theta"]),

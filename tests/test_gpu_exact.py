@@ -116,6 +116,34 @@ def test_exact_edge_cases(lib):
         lib.ef_circuit_destroy(h)
 
 
+def test_host_calls_leave_outputs_untouched_on_out_of_range_bits(lib):
+    """A bitstring with a bit at or above n_modes makes the host-pointer calls
+    return EF_EINVAL and leaves every output array as it was (the range check
+    runs while the GPU works; nothing is copied back)."""
+    import ctypes
+    c, bits = W.brick8_exact()
+    b = np.ascontiguousarray(np.concatenate([bits[:5], np.array([W.modes_to_bits([0, 1, 2, 9])],
+                                                                dtype=np.uint64)]))
+    L = lib.load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    bp = b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_AUTO)
+    try:
+        out, err, se = (np.full(len(b), 7.0) for _ in range(3))
+        rc = L.ef_prob_exact(h, bp, len(b), out.ctypes.data_as(dp), err.ctypes.data_as(dp))
+        assert rc == lib.EF_EINVAL
+        assert np.all(out == 7.0) and np.all(err == 7.0)
+        rc = L.ef_prob_approx(h, bp, len(b), 64, 3, 0, out.ctypes.data_as(dp), se.ctypes.data_as(dp),
+                              err.ctypes.data_as(dp))
+        assert rc == lib.EF_EINVAL
+        assert np.all(out == 7.0) and np.all(se == 7.0) and np.all(err == 7.0)
+        # the circuit stays usable
+        p = lib.ef_prob_exact(h, bits[:5])
+        assert np.max(np.abs(p - O.exact_probabilities(c, bits[:5]))) <= 1e-5
+    finally:
+        lib.ef_circuit_destroy(h)
+
+
 def test_exact_wrong_spin_sector_is_zero(lib):
     c = W.lucj_circuit(5, 2, 2, 1, n_onsite=3, n_same=2, angle_sampler=W.normal_var(0.5), seed=8)
     bits = np.array([W.modes_to_bits([0, 1, 2, 5]), W.modes_to_bits([0, 5, 6, 7])], dtype=np.uint64)
