@@ -38,6 +38,29 @@ def test_estimate_matches_oracle_estimate(lib):
     assert np.max(np.abs(se - se_ref) / np.maximum(se_ref, floor)) <= 1e-8
 
 
+def test_estimate_matches_oracle_on_spread_outcomes_across_2_32(lib):
+    """The same parity on outcomes whose probabilities run from 0.64 down to
+    1.2e-4 (a 10-mode random circuit, extent 14.6), at global indices that
+    cross 2^32 and with a seed that fills both key words."""
+    c = W.random_fig4_circuit(10, 4, 7, 3, seed=31, angle_std=1.2)
+    bits = W.sector_bitstrings_all(10, 4)
+    pe = O.exact_probabilities(c, bits)
+    pick = np.argsort(-pe)[[0, 3, 8, 14]]
+    sub = bits[pick]
+    eps, delta, seed, base = 0.05, 0.05, 0xFEDC_BA98_7654_3210, (1 << 32) - 2
+    p_ref, se_ref, t_ref = O.estimate(c, sub, eps, delta, seed, b_indices=[base + i for i in range(len(sub))])
+    h = lib.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=lib.EF_PREC_FP64)
+    try:
+        p, se, t = lib.ef_prob_estimate(h, sub, eps, delta, seed=seed, index_base=base)
+    finally:
+        lib.ef_circuit_destroy(h)
+    floor = 1e-6 / math.comb(10, 4)
+    assert np.array_equal(t, t_ref)
+    assert np.max(np.abs(p - p_ref) / np.maximum(p_ref, floor)) <= 1e-10
+    assert np.max(np.abs(se - se_ref) / np.maximum(se_ref, floor)) <= 1e-8
+    assert np.all(np.abs(p - pe[pick]) <= eps)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "auto"])
 def test_estimate_guarantee_over_seeds(lib, prec):
     c = W.lucj_circuit(6, 3, 3, 1, n_onsite=6, n_same=3, angle_sampler=W.normal_var(0.1), seed=7)
