@@ -21,6 +21,7 @@ CPU oracle (run in the CPU-baseline worker pool):
                          FP64 single-circuit form of the same circuits
   config5_lucj40_grad    gradient of sum_b w_b log p_b, 4096 bitstrings, 2412 angles
   fig4_latency           single-outcome Exact latency, random circuits of 8-36 qubits, k 16
+  estimate_lucj52        Estimate (eps = delta = 0.01) on 10^4 bitstrings of the 52-qubit workload
   peaks                  measured FP32 / FP64 FMA and Philox4x32-10 rates of this GPU
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -564,6 +565,44 @@ def bench_fig4(ef, torch, dev, stream, flush):
                         "sector bitstring, Exact", "rows": rows}
 
 
+def eq6_count(eps: float, delta: float, pmax: float, xi: float) -> int:
+    """Eq. 6: trajectories for |p_hat - p| <= eps with failure probability at most
+    delta when p <= p_max (for comparison with what the Estimate rounds spend)."""
+    num = (math.sqrt(xi) + math.sqrt(pmax)) ** 2
+    den = (math.sqrt(pmax + eps) - math.sqrt(pmax)) ** 2
+    return int(math.ceil(2.0 * num / den * math.log(2.0 * math.e * math.e / delta)))
+
+
+def bench_estimate(ef, n_bits: int = 10_000, eps: float = 1e-2, delta: float = 1e-2):
+    """Estimate (Section III-A) on 10^4 bitstrings of the 52-qubit LUCJ workload,
+    EF_PREC_AUTO: host wall time of the synchronous ef_prob_estimate call (the
+    copies, every round's Raw Estimate launches and the host steps between
+    rounds included), and the trajectories its rounds spend against one Raw
+    Estimate at p_max = 1."""
+    c, bits = W.lucj52_approx(n_bits)
+    h = ef.ef_circuit_create(c.n_modes, c.occupation, c.gates, precision=ef.EF_PREC_AUTO, tol=1e-5)
+    try:
+        xi = ef.ef_circuit_extent(h)
+        ef.ef_prob_estimate(h, bits, eps, delta, seed=1)  # warm-up (workspace allocation)
+        walls, spent = [], None
+        for s in range(2):
+            t0 = time.perf_counter()
+            p, se, spent = ef.ef_prob_estimate(h, bits, eps, delta, seed=2 + s)
+            walls.append(time.perf_counter() - t0)
+    finally:
+        ef.ef_circuit_destroy(h)
+    wall = statistics.mean(walls)
+    return {"workload": f"Estimate, eps = {eps}, delta = {delta}, on {n_bits} sector bitstrings of the 52-qubit "
+                        f"LUCJ workload (k = 152, extent {xi:.3f}), EF_PREC_AUTO",
+            "value": n_bits / wall, "unit": UNIT, "ms_per_call": 1e3 * wall, "steps": len(walls), "warmup": 1,
+            "timing": "host wall clock of the synchronous call (copies and host steps between rounds included)",
+            "trajectories_per_bitstring_mean": float(np.mean(spent)),
+            "trajectories_per_bitstring_max": int(np.max(spent)),
+            "one_shot_eq6_at_pmax_1": eq6_count(eps, delta, 1.0, xi),
+            "trajectories_per_s": float(np.sum(spent)) / wall,
+            "max_p_hat": float(np.max(p))}
+
+
 # ----------------------------------------------------------------------------- headline arm
 
 
@@ -721,6 +760,10 @@ def run_ours(args):
         line["fig4_latency"] = bench_fig4(ef, torch, dev, stream, flush)
         line["config3_lucj52_approx"] = bench_config3(ef, torch, dev, stream, flush, pool, peaks)
         line["config4_batch64"] = bench_config4(ef, torch, dev, stream, flush, pool, peaks)
+        try:
+            line["estimate_lucj52"] = bench_estimate(ef)
+        except Exception as e:  # reported in the line; never costs the line itself
+            line["estimate_lucj52"] = {"error": f"{type(e).__name__}: {e}"}
     if pool is not None:
         pool.close()
     if rank == 0:
