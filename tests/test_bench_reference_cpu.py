@@ -1,7 +1,10 @@
 """The bench's reference arm on CPU: `bench.py --impl reference` times the FP64
 oracle on the host cores and prints one JSON line with the same metric, unit
-and workload as the CUDA arm; under a multi-rank launch only rank 0 works."""
+and workload as the CUDA arm; under a multi-rank launch only rank 0 works.
+Also the host logic of the CUDA arm's Estimate sub-object, with a stand-in
+for the binding."""
 import json
+import math
 import os
 import subprocess
 import sys
@@ -57,3 +60,35 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert _json_lines(r.stdout) == []
+
+
+def test_estimate_sub_object_shape_with_a_stand_in_binding():
+    """The Estimate sub-object's host logic (no GPU): a stand-in for the
+    binding returns fixed trajectory counts; the sub-object reports them with
+    the Eq. 6 count of one Raw Estimate at p_max = 1 beside them."""
+    import numpy as np
+
+    import bench
+
+    class StandIn:
+        EF_PREC_AUTO = 2
+
+        def ef_circuit_create(self, n, occ, gates, precision=0, tol=0.0):
+            return object()
+
+        def ef_circuit_extent(self, h):
+            return 4.0
+
+        def ef_prob_estimate(self, h, bits, eps, delta, seed=0, index_base=0):
+            n = len(bits)
+            return np.zeros(n), np.zeros(n), np.full(n, 1000, dtype=np.int64)
+
+        def ef_circuit_destroy(self, h):
+            pass
+
+    d = bench.bench_estimate(StandIn(), n_bits=50)
+    assert d["unit"] == bench.UNIT and d["value"] > 0 and d["steps"] == 2
+    assert d["trajectories_per_bitstring_mean"] == 1000 and d["trajectories_per_bitstring_max"] == 1000
+    # Eq. 6 at p_max = 1, eps = delta = 0.01, extent 4: 2 (2 + 1)^2 / (sqrt(1.01) - 1)^2 log(2 e^2 / 0.01)
+    want = math.ceil(2 * 9 / (math.sqrt(1.01) - 1) ** 2 * math.log(2 * math.e ** 2 / 0.01))
+    assert d["one_shot_eq6_at_pmax_1"] == want
