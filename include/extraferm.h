@@ -86,7 +86,10 @@ typedef struct {
 
 typedef enum {
     EF_PREC_FP64 = 0,       /* minors, LU and accumulation in FP64 */
-    EF_PREC_FP32_MINOR = 1, /* minors and LU in FP32, branch sum in FP64 */
+    EF_PREC_FP32_MINOR = 1, /* minors and LU in FP32; Exact branch sums in float-pair
+                               arithmetic (about 48 bits); Raw Estimate: per-bitstring
+                               tables (A0, its inverse, K) in FP64, trajectory terms
+                               in FP32 summed in float pairs */
     EF_PREC_AUTO = 2        /* FP32 minors; Exact: for results whose error estimate
                                exceeds tol the determinants carrying most of the
                                estimated error are redone in float-pair arithmetic
@@ -105,7 +108,7 @@ typedef struct {
     int32_t precision;         /* ef_precision; default EF_PREC_AUTO */
     int32_t flags;             /* EF_FLAG_* */
     double tol;                /* relative-error target of EF_PREC_AUTO, default 1e-5 */
-    int32_t tile_override[4];  /* 0 = automatic; [0] = FP32 Exact sub-branches per chunk (log2);
+    int32_t tile_override[4];  /* 0 = automatic; [0] = FP32 Exact flip patterns per chunk (log2);
                                   [1] = constant K of the FP32 error estimate in tenths (default 40) */
 } ef_options;
 
@@ -166,8 +169,9 @@ int ef_circuit_set_precision(ef_circuit* c, int32_t precision, double tol);
  * negated). nb = 0 is allowed. The circuit's 2^k trajectories are enumerated
  * per independent mode block as distinct flip patterns; controlled-phase
  * gates whose modes no Givens rotation touches before them, or after them,
- * change no probability and are left out. k per block is limited by device
- * memory (EF_EUNSUPPORTED beyond 2^24 sub-branches per block). */
+ * change no probability and are left out. EF_EUNSUPPORTED beyond 2^22 flip
+ * patterns, 22 enumerated controlled-phase gates or 32 particles in a mode
+ * block, or 12 controlled-phase gates shared by two blocks. */
 int ef_prob_exact(ef_circuit* c, const uint64_t* bits, int64_t nb, double* out, double* err_out);
 int ef_prob_exact_dev(ef_circuit* c, const uint64_t* d_bits, int64_t nb, double* d_out,
                       double* d_err_out, void* stream);
